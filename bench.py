@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark of the semi-implicit Fourier-spectral phase-field step on GB300.
+
+Workload (default): 2D periodic 1024 x 1024 grid, c plus two order parameters
+(p = 2), FP32 fields and transforms, seeded uniform noise +-0.01 about
+c = eta = 0.5, dt = 6 x the explicit-FD stable dt, the paper's parameters.
+One timed "step" is one time step of Algorithm 1 (row pass + column pass)
+through the C ABI, with the L2 cache flushed (a 512 MB buffer written)
+before every timed step.  The FP64 step of the same workload is timed the same
+way and reported beside it.
+
+Output: one JSON line on rank 0 (see the keys at the end of main()).
+  --impl reference times the CPU oracle (the plain FP64 C++ solver) on the
+  host cores on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank runs an independent replica (the step has no
+exchange between simulations); value = all ranks' grid-point-steps / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FS grid-point-steps/s & % HBM roofline, FP32/batched vs plain FP64, 1 GB300"
+UNIT = "grid-point-steps/s"
+GRID = (1024, 1024)
+P = 2
+WORKLOAD = "2D periodic 1024x1024, c + 2 eta, FP32, dt = 6 x FD-stable dt, seeded +-0.01 noise"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def problem():
+    from paper_2306_04322_gb300 import inputs as I
+    pr = I.Problem(n=GRID, p=P)
+    pr.dt = 6.0 * I.fd_stable_dt(pr)
+    return pr
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dram_traffic(kernel: str, precision: str):
+    """DRAM bytes per launch from the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "traffic_2d_1024_p2.txt")
+    try:
+        for line in open(path):
+            parts = line.split()
+            if len(parts) >= 4 and parts[0] == "traffic" and parts[1] == kernel and parts[2] == precision:
+                return float(parts[3])
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def time_gpu(precision: str, steps: int, warmup: int, device: int):
+    """Device time of `steps` single time steps, L2 flushed before each."""
+    import torch
+    from paper_2306_04322_gb300 import fs, inputs as I
+    pr = problem()
+    dtype = torch.float64 if precision == "f64" else torch.float32
+    f0 = torch.tensor(I.noise_fields(pr, seed=0), dtype=dtype, device=f"cuda:{device}")
+    plan = fs.Plan(pr, precision)
+    plan.set_fields(f0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{device}")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush.zero_()
+        fs.fs_step_async(plan.h, 1)
+    fs.fs_profile_read(plan.h)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        fs.fs_step_profiled(plan.h, 1)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    kern_ms, kern_cnt = fs.fs_profile_read(plan.h)
+    launches = sum(kern_cnt)
+    ws = plan.workspace_bytes
+    plan.close()
+    return {"total_ms": total_ms, "kern_ms": kern_ms, "kern_cnt": kern_cnt, "launches": launches,
+            "workspace_bytes": ws, "npts": pr.npoints}
+
+
+def time_e2e(steps: int, warmup: int, device: int):
+    """Through the C ABI with pinned host buffers: per step, copy the fields in,
+    one time step, copy the fields out."""
+    import torch
+    from paper_2306_04322_gb300 import fs, inputs as I
+    pr = problem()
+    host_in = torch.tensor(I.noise_fields(pr, seed=0), dtype=torch.float32).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    plan = fs.Plan(pr, "f32")
+    ins = [host_in[f] for f in range(pr.nf)]
+    outs = [host_out[f] for f in range(pr.nf)]
+    for _ in range(warmup):
+        fs.fs_set_fields(plan.h, ins)
+        fs.fs_step_async(plan.h, 1)
+        fs.fs_get_fields(plan.h, outs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        fs.fs_set_fields(plan.h, ins)
+        fs.fs_step_async(plan.h, 1)
+        fs.fs_get_fields(plan.h, outs)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    plan.close()
+    nbytes = host_in.numel() * 4
+    return {"seconds": dt, "npts": pr.npoints, "h2d": nbytes, "d2h": nbytes}
+
+
+def cpu_baseline(seconds: float):
+    """The oracle (plain FP64 C++ solver) on the host cores, bounded sample:
+    whole time steps of the same workload until `seconds` have passed."""
+    from oracle import oracle as O
+    from paper_2306_04322_gb300 import inputs as I
+    pr = problem()
+    cores = os.cpu_count() or 1
+    used = O.set_threads(cores)
+    f = I.noise_fields(pr, seed=0)
+    O.step(pr, f, 1)  # warm (page-in, tables)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        f, _ = O.step(pr, f, 1)
+        n += 1
+        if time.perf_counter() - t0 >= seconds and n >= 2:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": pr.npoints * n / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{n} whole FP64 oracle time steps of the 1024x1024 p=2 workload "
+                      f"({dt:.1f} s, OpenMP over FFT lines, {used} threads)"}
+
+
+def reference_arm(args):
+    world, rank, local = dist_info()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2306_04322_gb300 import inputs as I
+    pr = problem()
+    cores = os.cpu_count() or 1
+    used = O.set_threads(cores)
+    f = I.noise_fields(pr, seed=0)
+    for _ in range(args.warmup):
+        f, _ = O.step(pr, f, 1)
+    budget = 150.0
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(args.steps):
+        f, _ = O.step(pr, f, 1)
+        done += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    per = dt / done
+    total = per * args.steps
+    value = pr.npoints * args.steps / total
+    sample = (f"{done} of {args.steps} whole FP64 oracle time steps timed "
+              f"({'all' if done == args.steps else 'time-bounded sample, per-step time extrapolated'}), "
+              f"{used} threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("FP32", "FP64 (oracle)"), "grid": list(GRID), "p": P},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_info()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    from paper_2306_04322_gb300 import build as B
+    from paper_2306_04322_gb300 import fs
+    B.build()
+    fs.lib()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        r32 = time_gpu("f32", args.steps, args.warmup, local)
+    barrier()
+    r64 = time_gpu("f64", args.steps, args.warmup, local)
+    barrier()
+    e2e = time_e2e(args.steps, args.warmup, local)
+    barrier()
+
+    t32 = max_over_ranks(r32["total_ms"]) / 1e3
+    t64 = max_over_ranks(r64["total_ms"]) / 1e3
+    te2e = max_over_ranks(e2e["seconds"])
+    npts = r32["npts"]
+    value = world * npts * args.steps / t32
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = load_peaks()
+    s = 4
+    nf = 1 + P
+    names = ["fs_row_kernel", "fs_col_kernel"]
+    # algorithmic bytes per launch (steady state): row pass reads nf half
+    # spectra (nf N s bytes) and writes nf + 1 (2D, N/2 complex each);
+    # column pass reads nf + 1 and writes nf.
+    alg = [(2 * nf + 1) * npts * s, (2 * nf + 1) * npts * s]
+    avg_ms = [m / max(c, 1) for m, c in zip(r32["kern_ms"], r32["kern_cnt"])]
+    dom = max(range(len(avg_ms)), key=lambda i: r32["kern_ms"][i])
+    achieved = alg[dom] / (avg_ms[dom] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind,
+            "traffic": dram_traffic(names[dom], "f32"),
+            "alg_bytes_per_launch": alg[dom], "avg_launch_ms": avg_ms[dom],
+            "kernels": {n: {"avg_ms": a, "launches": c, "share": m / max(sum(r32["kern_ms"]), 1e-30)}
+                        for n, a, c, m in zip(names, avg_ms, r32["kern_cnt"], r32["kern_ms"])}}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t32 * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(GRID), "p": P, "dt": problem().dt,
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "workspace_bytes": r32["workspace_bytes"]},
+        "roofline": roof,
+        "e2e": {"value": world * npts * args.steps / te2e, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
+                "d2h_bytes_per_step": e2e["d2h"],
+                "how": "fs_set_fields from pinned host + fs_step_async(1) + fs_get_fields to pinned host, "
+                       "wall clock"},
+        "gpu_launches": r32["launches"],
+        "clocks": clk.summary(),
+        "fp64": {"value": world * npts * args.steps / t64, "unit": UNIT, "ms_per_step": t64 * 1e3 / args.steps,
+                 "kernels_ms": r64["kern_ms"], "launches": r64["launches"]},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * fs.h -- C ABI of the GB300 (sm_103a) semi-implicit Fourier-spectral
+ * phase-field library.
+ *
+ * The library advances the coupled Cahn-Hilliard / Allen-Cahn model of
+ * Boccardo, Tong, Leen, Tourret and Segurado, "Efficiency and accuracy of
+ * GPU-parallelized Fourier spectral methods for solving phase-field models"
+ * (arXiv 2306.04322):
+ *   - free energy and chemical free-energy density f_chem: Section 2.1,
+ *     Eq. (fe) and the definitions of f_alpha, f_beta, h and g after it;
+ *   - evolution equations: Eqs. (C-H) and (A-C), periodic boundaries;
+ *   - semi-implicit time discretisation: Eqs. (C-H_discrete), (A-C_discrete);
+ *   - Fourier-space solve: Eqs. (C-H_discrete_fft), (A-C_discrete_fft),
+ *     independent terms (C-H_fft_b), (A-C_fft_b), per-mode inversion
+ *     (A-C_discrete_fft_c), (A-C_discrete_fft_eta);
+ *   - squared frequency norm: Eqs. (Gamma_fft), (Gamma_fft_3d); FS-FD forms
+ *     (Gamma_fft-fdO2), (Gamma_fft-fdO4) and their 3D versions;
+ *   - the time loop: Algorithm 1 ("FS solution algorithm");
+ *   - the explicit finite-difference comparison scheme: Section 2.2
+ *     (forward Euler, 5-point / 7-point Laplacian, periodic boundaries).
+ *
+ * Conventions shared by every call:
+ *   - Fields: nf = 1 + p real arrays, order c, eta_1 .. eta_p.  Each field is
+ *     one contiguous array of N = nx*ny*nz values, x fastest:
+ *     idx = (z*ny + y)*nx + x.  The element type is double for FS_F64 and
+ *     float for every FS_F32* precision.
+ *   - Pointers passed in and out may be device memory or host memory
+ *     (pinned or pageable); copies use cudaMemcpyDefault.  The caller owns
+ *     them; a plan keeps no caller pointer after a call returns.
+ *   - Every call is ordered on the plan's CUDA stream.  Calls on one plan
+ *     must not run concurrently from several host threads.
+ *   - Grid sizes: each axis a power of two in [8, 1024].  Other sizes return
+ *     FS_ERR_UNSUPPORTED.  p in [0, 4].  dt > 0; M = 0 or L = 0 is allowed.
+ *   - Status codes are returned by value; fs_last_error() gives the text of
+ *     the last failure on that plan (or on this thread for a NULL plan).
+ */
+#ifndef FS_H_
+#define FS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fs_plan* fs_plan_t; /* opaque; owns all device workspace */
+
+typedef enum {
+  FS_OK = 0,
+  FS_ERR_INVALID_ARG = 1, /* NULL pointer, bad value (dt <= 0, p out of range, ...) */
+  FS_ERR_UNSUPPORTED = 2, /* valid request this build does not implement (size, combination) */
+  FS_ERR_OOM = 3,         /* device workspace allocation failed */
+  FS_ERR_CUDA = 4,        /* a CUDA runtime call failed; see fs_last_error */
+  FS_ERR_NONFINITE = 5,   /* a NaN / Inf appeared in the fields during fs_step */
+  FS_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+  FS_ERR_STATE = 7        /* call out of order (e.g. fs_step before fs_set_fields) */
+} fs_status;
+
+typedef enum {
+  FS_F64 = 0,          /* FP64 fields, transforms and update */
+  FS_F32 = 1,          /* FP32 fields and transforms; mean(c) carried in FP64 */
+  FS_F32_TC_TF32 = 2,  /* FP32 with one DFT stage on tensor cores (TF32) */
+  FS_F32_TC_BF16X3 = 3 /* FP32 with one DFT stage on tensor cores (split BF16, 3 products) */
+} fs_precision;
+
+typedef enum {
+  FS_LAP_SPECTRAL = 0, /* |xi|^2, Eqs. (Gamma_fft), (Gamma_fft_3d) */
+  FS_LAP_FD2 = 1,      /* |xi_c2|^2, Eqs. (Gamma_fft-fdO2) and 3D form */
+  FS_LAP_FD4 = 2       /* |xi_c4|^2, Eqs. (Gamma_fft-fdO4) and 3D form */
+} fs_laplacian;
+
+typedef enum {
+  FS_SCHEME_SEMI_IMPLICIT_FS = 0, /* Algorithm 1 */
+  FS_SCHEME_EXPLICIT_FD = 1       /* Section 2.2 comparison scheme (2D only) */
+} fs_scheme;
+
+/* Problem description.  Physical parameters follow Section 2.1 (benchmark
+ * values: kappa_c = kappa_eta = 3, rho2 = 2, c_alpha = 0.3, c_beta = 0.7,
+ * w = 1, alpha = 5, M = L = 5); grid and dt follow the initialisation block
+ * of Algorithm 1.  n[d] and dx[d] for d >= ndim are ignored. */
+typedef struct {
+  int ndim;     /* 2 or 3 */
+  int n[3];     /* points along x, y, z */
+  double dx[3]; /* spacing along x, y, z (> 0); domain length l = n dx */
+  int p;        /* number of order parameters, 0..4 */
+  double M, L, kappa_c, kappa_eta, rho2, c_alpha, c_beta, w, alpha, dt;
+  int precision; /* fs_precision */
+  int lap;       /* fs_laplacian */
+  int scheme;    /* fs_scheme */
+} fs_params;
+
+/* Optional device-memory allocator used for all plan workspace.  NULL
+ * functions select cudaMalloc / cudaFree.  alloc returns NULL on failure. */
+typedef void* (*fs_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*fs_free_fn)(void* ptr, void* ctx);
+
+/* Create a plan for one simulation.  `stream` is a cudaStream_t (NULL: the
+ * legacy default stream).  Validates prm first (no CUDA call is made for an
+ * invalid request), then allocates the workspace: nf real fields plus
+ * (nf + 1) packed half-spectrum slots of N/2 complex values, and small
+ * per-axis tables.  On failure *out is NULL. */
+fs_status fs_plan_create(const fs_params* prm, void* stream, fs_plan_t* out);
+fs_status fs_plan_create_ex(const fs_params* prm, void* stream, fs_alloc_fn alloc, fs_free_fn dealloc,
+                            void* ctx, fs_plan_t* out);
+
+/* Batched ensemble: `count` independent 2D simulations with their own grid
+ * sizes and parameters (each[i]), one plan, one launch per pass for all of
+ * them.  All members share precision and p; lap and scheme must be
+ * spectral FS.  Field pointer arrays for a batch plan are member-major:
+ * fields[i * nf + f]. */
+fs_status fs_batch_create(const fs_params* each, int count, void* stream, fs_plan_t* out);
+
+/* Copy the state in: fields[f] points to field f (nf pointers, plan dtype).
+ * Also computes sum(c) in FP64 for the mean-mode carry of FP32 plans. */
+fs_status fs_set_fields(fs_plan_t plan, const void* const* fields);
+
+/* Advance nsteps >= 0 time steps (Algorithm 1 iterations, or explicit FD
+ * steps for FS_SCHEME_EXPLICIT_FD).  Launches asynchronously, then
+ * synchronises the stream and returns FS_ERR_NONFINITE if a non-finite value
+ * was met.  Long runs replay a captured CUDA graph of the step. */
+fs_status fs_step(fs_plan_t plan, int64_t nsteps);
+
+/* As fs_step, without the final synchronisation and status read. */
+fs_status fs_step_async(fs_plan_t plan, int64_t nsteps);
+
+/* Synchronise the plan's stream and return the sticky device status. */
+fs_status fs_sync(fs_plan_t plan);
+
+/* Copy the current real fields out (nf pointers).  Materialises them first
+ * when the state is held as spectra (one inverse row pass). */
+fs_status fs_get_fields(fs_plan_t plan, void* const* fields_out);
+
+/* Replace the physical parameters and dt of an existing plan.  Grid, p,
+ * precision, lap and scheme must match the plan; the state is kept. */
+fs_status fs_set_params(fs_plan_t plan, const fs_params* prm);
+
+/* Rebind the plan to another stream. */
+fs_status fs_set_stream(fs_plan_t plan, void* stream);
+
+/* Total free energy, Eq. (fe), of the current state (rectangle rule, dV =
+ * prod dx, gradient terms through Parseval with the plan's |xi|^2).
+ * parts (may be NULL) receives 2 + p values: chemical, c-gradient and each
+ * eta_i-gradient contribution.  Synchronises. */
+fs_status fs_free_energy(fs_plan_t plan, double* F, double* parts);
+
+/* Adjoint of one step linearised at the state u (nf real field pointers, plan
+ * dtype, device memory): lambda_out = J(u)^T lambda_in, and grad_theta[0..3]
+ * += d<lambda_in, step(u)>/d(M, L, kappa_c, kappa_eta).  The paper has no
+ * adjoint; this is the transpose of the Jacobian of the Algorithm-1 step.
+ * Uses the plan's workspace (the plan's own state is not modified).
+ * Synchronises when grad_theta is not NULL. */
+fs_status fs_step_adjoint(fs_plan_t plan, const void* const* u, const void* const* lambda_in,
+                          void* const* lambda_out, double grad_theta[4]);
+
+/* Diagnostic timing: as fs_step_async with eager launches (no graph) and a
+ * CUDA event pair recorded around every pass launch on the plan's stream.
+ * fs_profile_read synchronises, writes the summed milliseconds and the launch
+ * count of each pass kind since the last read to ms_per_pass[] and
+ * launches_per_pass[] (may be NULL), at most npass_max entries, sets *npass
+ * (2D: 0 row pass, 1 column pass) and returns the sticky device status. */
+fs_status fs_step_profiled(fs_plan_t plan, int64_t nsteps);
+fs_status fs_profile_read(fs_plan_t plan, double* ms_per_pass, int64_t* launches_per_pass, int npass_max,
+                          int* npass);
+
+/* Device bytes owned by the plan. */
+fs_status fs_workspace_bytes(fs_plan_t plan, size_t* bytes);
+
+/* Number of kernel launches issued by the last fs_step / fs_step_async. */
+fs_status fs_last_launch_count(fs_plan_t plan, int64_t* launches);
+
+/* Free everything the plan owns.  NULL is accepted. */
+fs_status fs_destroy(fs_plan_t plan);
+
+/* Text of the last error on `plan` (thread-local text for a NULL plan). */
+const char* fs_last_error(fs_plan_t plan);
+
+/* Library version string. */
+const char* fs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FS_H_ */

@@ -1,0 +1,42 @@
+// Internal declarations shared by the plan layer (fs_plan.cu) and the kernel
+// translation units.  Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fs {
+
+enum : int { FS_FLAG_NONFINITE = 1, FS_FLAG_TIMEOUT = 2, FS_FLAG_BOUNDS = 4 };
+
+// Arguments of one pass over one simulation (passed by value).
+struct KArgs {
+  void* spec;              // packed half spectra: slots of slot_stride complex values
+  void* real;              // real fields: nf arrays of npts values
+  const void* tw;          // master twiddle table (complex, plan precision)
+  const double* k2x;       // |xi_x|^2 per x bin, nx/2 + 1 entries
+  const double* k2y;       // |xi_y|^2 per y bin, ny entries
+  const double* k2z;       // |xi_z|^2 per z bin, nz entries (3D)
+  long long slot_stride;   // complex values per spectrum slot
+  long long npts;          // real points per field
+  int nx, ny, nz, nf;
+  long long lines;         // rows handled by a row pass (ny * nz)
+  int mode;                // row pass: 0 step from spectra, 1 step from real, 2 inverse only
+  double M, L, kappa_c, kappa_eta, rho2, c_alpha, c_beta, w, alpha, dt;
+  double scale;            // k-space scale 1 / (2 N)
+  double inv_npts;         // 1 / N
+  const double* csum;      // FP64 sum of c carried for the k = 0 mode (NULL: off)
+  int* flag;               // sticky error bits (FS_FLAG_*)
+};
+
+// Kernel launchers, one per precision (fs_k2d_f32.cu / fs_k2d_f64.cu).
+// Return cudaErrorInvalidValue for a size without an instantiation.
+cudaError_t row_launch_f32(const KArgs& a, cudaStream_t s);
+cudaError_t row_launch_f64(const KArgs& a, cudaStream_t s);
+cudaError_t col_launch_f32(const KArgs& a, cudaStream_t s);
+cudaError_t col_launch_f64(const KArgs& a, cudaStream_t s);
+// FP64 sum of n values of x (float or double) added into *out.
+cudaError_t sum_launch_f32(const void* x, long long n, double* out, cudaStream_t s);
+cudaError_t sum_launch_f64(const void* x, long long n, double* out, cudaStream_t s);
+
+}  // namespace fs

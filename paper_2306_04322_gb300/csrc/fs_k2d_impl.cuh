@@ -1,0 +1,104 @@
+// Launch dispatch for the 2D row / column kernels of one precision.
+#pragma once
+
+#include "fs_kernels.cuh"
+
+namespace fs {
+
+// Opt a kernel into the full dynamic shared-memory size once per device.
+template <typename K>
+cudaError_t allow_big_smem(K kernel, unsigned* done_mask) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  unsigned bit = 1u << (dev & 31);
+  if (__atomic_load_n(done_mask, __ATOMIC_ACQUIRE) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) __atomic_fetch_or(done_mask, bit, __ATOMIC_RELEASE);
+  return e;
+}
+
+template <typename T, int NX>
+cudaError_t row_launch_n(const KArgs& a, cudaStream_t s) {
+  using Cfg = RowCfg<T, NX>;
+  long long rpc = Cfg::THREADS / Cfg::TPL;
+  if (rpc > a.lines) rpc = a.lines;
+  size_t smem = (size_t)rpc * (a.nf + 1) * Cfg::PL * sizeof(cplx<T>);
+  static unsigned done = 0;
+  cudaError_t e = allow_big_smem(fs_row_kernel<T, NX>, &done);
+  if (e != cudaSuccess) return e;
+  fs_row_kernel<T, NX><<<(unsigned)(a.lines / rpc), (unsigned)(rpc * Cfg::TPL), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int NY>
+cudaError_t col_launch_n(const KArgs& a, cudaStream_t s) {
+  using Cfg = ColCfg<T, NY>;
+  int Lh = a.nx / 2;
+  int tk = Cfg::TK < Lh ? Cfg::TK : Lh;
+  size_t smem = (size_t)NY * tk * sizeof(cplx<T>);
+  static unsigned done = 0;
+  cudaError_t e = allow_big_smem(fs_col_kernel<T, NY>, &done);
+  if (e != cudaSuccess) return e;
+  fs_col_kernel<T, NY><<<(unsigned)(Lh / tk), (unsigned)(tk * Cfg::TPL), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t row_launch_t(const KArgs& a, cudaStream_t s) {
+  switch (a.nx) {
+    case 8: return row_launch_n<T, 8>(a, s);
+    case 16: return row_launch_n<T, 16>(a, s);
+    case 32: return row_launch_n<T, 32>(a, s);
+    case 64: return row_launch_n<T, 64>(a, s);
+    case 128: return row_launch_n<T, 128>(a, s);
+    case 256: return row_launch_n<T, 256>(a, s);
+    case 512: return row_launch_n<T, 512>(a, s);
+    case 1024: return row_launch_n<T, 1024>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t col_launch_t(const KArgs& a, cudaStream_t s) {
+  switch (a.ny) {
+    case 8: return col_launch_n<T, 8>(a, s);
+    case 16: return col_launch_n<T, 16>(a, s);
+    case 32: return col_launch_n<T, 32>(a, s);
+    case 64: return col_launch_n<T, 64>(a, s);
+    case 128: return col_launch_n<T, 128>(a, s);
+    case 256: return col_launch_n<T, 256>(a, s);
+    case 512: return col_launch_n<T, 512>(a, s);
+    case 1024: return col_launch_n<T, 1024>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// FP64 sum reduction (grid-stride, warp shuffles, one atomic per CTA).
+template <typename T>
+__global__ void __launch_bounds__(256) fs_sum_kernel(const T* __restrict__ x, long long n, double* out) {
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += (double)x[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    atomicAdd(out, t);
+  }
+}
+
+template <typename T>
+cudaError_t sum_launch_t(const void* x, long long n, double* out, cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 1216) blocks = 1216;
+  if (blocks < 1) blocks = 1;
+  fs_sum_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const T*>(x), n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace fs

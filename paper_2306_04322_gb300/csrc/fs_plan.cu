@@ -1,0 +1,631 @@
+// C ABI of the semi-implicit Fourier-spectral phase-field library: plan
+// creation and validation, workspace ownership, state tracking, launch
+// sequencing and CUDA-graph replay of the time loop (Algorithm 1 of
+// Boccardo et al., arXiv 2306.04322).  Kernels live in the fs_k*.cu units.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fs.h"
+#include "fs_fft.cuh"
+#include "fs_internal.h"
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+enum StateKind { kStateNone = 0, kStateReal = 1, kStateSpec = 2, kStateBoth = 3 };
+
+struct Member {
+  fs_params prm;
+  long long npts = 0;
+  // device pointers into the plan's arena
+  void* spec = nullptr;
+  void* real = nullptr;
+  double* k2x = nullptr;
+  double* k2y = nullptr;
+  double* k2z = nullptr;
+  double* csum = nullptr;
+  long long slot_stride = 0;
+};
+
+}  // namespace
+
+struct fs_plan {
+  std::vector<Member> members;
+  bool f64 = true;
+  int nf = 1;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  fs_alloc_fn alloc = nullptr;
+  fs_free_fn dealloc = nullptr;
+  void* actx = nullptr;
+  std::vector<void*> blocks;
+  size_t ws_bytes = 0;
+  void* tw = nullptr;
+  int* flag = nullptr;
+  int* host_flag = nullptr;  // pinned
+  int state = kStateNone;
+  cudaGraphExec_t gexec = nullptr;
+  int gsteps = 0;
+  int64_t last_launches = 0;
+  std::vector<cudaEvent_t> ev_pool;  // fs_step_profiled timing events
+  std::vector<int> ev_kind;
+  size_t ev_used = 0;
+  std::string err;
+};
+
+namespace {
+
+fs_status fail(fs_plan* p, fs_status s, const std::string& msg) {
+  if (p)
+    p->err = msg;
+  else
+    g_thread_error = msg;
+  return s;
+}
+
+fs_status cuda_fail(fs_plan* p, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(p, FS_ERR_CUDA, m);
+}
+
+bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+fs_status validate(const fs_params* p, std::string* why) {
+  if (!p) {
+    *why = "params is NULL";
+    return FS_ERR_INVALID_ARG;
+  }
+  if (p->ndim != 2 && p->ndim != 3) {
+    *why = "ndim must be 2 or 3";
+    return FS_ERR_INVALID_ARG;
+  }
+  for (int d = 0; d < p->ndim; ++d) {
+    if (p->n[d] <= 0) {
+      *why = "grid size must be positive";
+      return FS_ERR_INVALID_ARG;
+    }
+    if (!finite_pos(p->dx[d])) {
+      *why = "dx must be finite and > 0";
+      return FS_ERR_INVALID_ARG;
+    }
+  }
+  if (p->p < 0 || p->p > 4) {
+    *why = "p must be in [0, 4]";
+    return FS_ERR_INVALID_ARG;
+  }
+  if (!finite_pos(p->dt)) {
+    *why = "dt must be finite and > 0";
+    return FS_ERR_INVALID_ARG;
+  }
+  const double nn[] = {p->M, p->L, p->kappa_c, p->kappa_eta, p->rho2, p->w, p->alpha};
+  for (double v : nn)
+    if (!finite_nonneg(v)) {
+      *why = "M, L, kappa_c, kappa_eta, rho2, w, alpha must be finite and >= 0";
+      return FS_ERR_INVALID_ARG;
+    }
+  if (!std::isfinite(p->c_alpha) || !std::isfinite(p->c_beta)) {
+    *why = "c_alpha, c_beta must be finite";
+    return FS_ERR_INVALID_ARG;
+  }
+  if (p->precision < FS_F64 || p->precision > FS_F32_TC_BF16X3) {
+    *why = "unknown precision";
+    return FS_ERR_INVALID_ARG;
+  }
+  if (p->lap < FS_LAP_SPECTRAL || p->lap > FS_LAP_FD4) {
+    *why = "unknown lap";
+    return FS_ERR_INVALID_ARG;
+  }
+  if (p->scheme < FS_SCHEME_SEMI_IMPLICIT_FS || p->scheme > FS_SCHEME_EXPLICIT_FD) {
+    *why = "unknown scheme";
+    return FS_ERR_INVALID_ARG;
+  }
+  for (int d = 0; d < p->ndim; ++d)
+    if (!pow2_in(p->n[d], 8, 1024)) {
+      *why = "each grid axis must be a power of two in [8, 1024]";
+      return FS_ERR_UNSUPPORTED;
+    }
+  if (p->ndim == 3) {
+    *why = "3D grids are not built in this library version";
+    return FS_ERR_UNSUPPORTED;
+  }
+  if (p->scheme != FS_SCHEME_SEMI_IMPLICIT_FS) {
+    *why = "explicit FD scheme is not built in this library version";
+    return FS_ERR_UNSUPPORTED;
+  }
+  if (p->precision == FS_F32_TC_TF32 || p->precision == FS_F32_TC_BF16X3) {
+    *why = "tensor-core DFT stage is not built in this library version";
+    return FS_ERR_UNSUPPORTED;
+  }
+  return FS_OK;
+}
+
+// Squared frequency norm contribution of bin k on an axis of n points and
+// spacing dx: spectral (Eq. Gamma_fft), FS-FD O(dl^2) (Eq. Gamma_fft-fdO2),
+// FS-FD O(dl^4) (Eq. Gamma_fft-fdO4); index vector [0..n/2, -(n/2-1)..-1].
+double axis_k2(int lap, int k, int n, double dx) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  int nk = k <= n / 2 ? k : k - n;
+  double xi = (double)(2.0L * pi * (long double)nk / ((long double)n * (long double)dx));
+  if (lap == FS_LAP_FD2) return -2.0 * (std::cos(dx * xi) - 1.0) / (dx * dx);
+  if (lap == FS_LAP_FD4) return -(16.0 * std::cos(dx * xi) - std::cos(2.0 * dx * xi) - 15.0) / (6.0 * dx * dx);
+  return xi * xi;
+}
+
+void* plan_alloc(fs_plan* p, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* ptr = nullptr;
+  if (p->alloc) {
+    ptr = p->alloc(bytes, p->actx);
+  } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+  }
+  if (ptr) {
+    p->blocks.push_back(ptr);
+    p->ws_bytes += bytes;
+  }
+  return ptr;
+}
+
+void plan_free_all(fs_plan* p) {
+  for (void* b : p->blocks) {
+    if (p->dealloc)
+      p->dealloc(b, p->actx);
+    else if (!p->alloc)
+      cudaFree(b);
+  }
+  p->blocks.clear();
+  p->ws_bytes = 0;
+}
+
+fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
+  fs::KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.spec = m.spec;
+  a.real = m.real;
+  a.tw = p->tw;
+  a.k2x = m.k2x;
+  a.k2y = m.k2y;
+  a.k2z = m.k2z;
+  a.slot_stride = m.slot_stride;
+  a.npts = m.npts;
+  a.nx = m.prm.n[0];
+  a.ny = m.prm.n[1];
+  a.nz = m.prm.ndim > 2 ? m.prm.n[2] : 1;
+  a.nf = p->nf;
+  a.lines = (long long)a.ny * a.nz;
+  a.mode = mode;
+  a.M = m.prm.M;
+  a.L = m.prm.L;
+  a.kappa_c = m.prm.kappa_c;
+  a.kappa_eta = m.prm.kappa_eta;
+  a.rho2 = m.prm.rho2;
+  a.c_alpha = m.prm.c_alpha;
+  a.c_beta = m.prm.c_beta;
+  a.w = m.prm.w;
+  a.alpha = m.prm.alpha;
+  a.dt = m.prm.dt;
+  a.scale = 1.0 / (2.0 * (double)m.npts);
+  a.inv_npts = 1.0 / (double)m.npts;
+  a.csum = p->f64 ? nullptr : m.csum;
+  a.flag = p->flag;
+  return a;
+}
+
+cudaError_t launch_row(const fs_plan* p, const fs::KArgs& a, cudaStream_t s) {
+  return p->f64 ? fs::row_launch_f64(a, s) : fs::row_launch_f32(a, s);
+}
+cudaError_t launch_col(const fs_plan* p, const fs::KArgs& a, cudaStream_t s) {
+  return p->f64 ? fs::col_launch_f64(a, s) : fs::col_launch_f32(a, s);
+}
+
+// One time step of every member: row pass then column pass.
+cudaError_t enqueue_step(fs_plan* p, int mode, cudaStream_t s, int64_t* launches) {
+  for (const Member& m : p->members) {
+    fs::KArgs a = make_args(p, m, mode);
+    cudaError_t e = launch_row(p, a, s);
+    if (e != cudaSuccess) return e;
+    e = launch_col(p, a, s);
+    if (e != cudaSuccess) return e;
+    *launches += 2;
+  }
+  return cudaSuccess;
+}
+
+void drop_graph(fs_plan* p) {
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  p->gexec = nullptr;
+  p->gsteps = 0;
+}
+
+constexpr int kGraphSteps = 32;
+
+cudaError_t build_graph(fs_plan* p) {
+  if (!p->cap_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  int64_t dummy = 0;
+  cudaError_t el = cudaSuccess;
+  for (int i = 0; i < kGraphSteps && el == cudaSuccess; ++i) el = enqueue_step(p, 0, p->cap_stream, &dummy);
+  e = cudaStreamEndCapture(p->cap_stream, &g);
+  if (el != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return el;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(&p->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return e;
+  p->gsteps = kGraphSteps;
+  return cudaSuccess;
+}
+
+fs_status read_flag(fs_plan* p) {
+  cudaError_t e = cudaMemcpyAsync(p->host_flag, p->flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+  if (e != cudaSuccess) return cuda_fail(p, e, "flag read");
+  e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(p, e, "stream synchronize");
+  int f = *p->host_flag;
+  if (f) {
+    cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream);
+    if (f & fs::FS_FLAG_TIMEOUT) return fail(p, FS_ERR_TIMEOUT, "a bounded device wait timed out");
+    if (f & fs::FS_FLAG_NONFINITE) return fail(p, FS_ERR_NONFINITE, "non-finite value in the fields");
+    return fail(p, FS_ERR_CUDA, "device reported an index out of bounds");
+  }
+  return FS_OK;
+}
+
+fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc_fn alloc, fs_free_fn dealloc,
+                        void* ctx, fs_plan_t* out) {
+  if (!out) return fail(nullptr, FS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!each || count <= 0) return fail(nullptr, FS_ERR_INVALID_ARG, "no simulations given");
+  for (int i = 0; i < count; ++i) {
+    std::string why;
+    fs_status s = validate(&each[i], &why);
+    if (s != FS_OK) return fail(nullptr, s, count > 1 ? "member " + std::to_string(i) + ": " + why : why);
+    if (each[i].precision != each[0].precision || each[i].p != each[0].p)
+      return fail(nullptr, FS_ERR_INVALID_ARG, "batch members must share precision and p");
+  }
+  if ((alloc == nullptr) != (dealloc == nullptr))
+    return fail(nullptr, FS_ERR_INVALID_ARG, "alloc and dealloc must both be given or both NULL");
+
+  fs_plan* p = new fs_plan();
+  p->f64 = each[0].precision == FS_F64;
+  p->nf = 1 + each[0].p;
+  p->stream = reinterpret_cast<cudaStream_t>(stream);
+  p->alloc = alloc;
+  p->dealloc = dealloc;
+  p->actx = ctx;
+  const size_t rs = p->f64 ? sizeof(double) : sizeof(float);
+  const size_t cs = 2 * rs;
+
+  // Workspace first (through the allocator hook), then tables.
+  p->members.resize(count);
+  for (int i = 0; i < count; ++i) {
+    Member& m = p->members[i];
+    m.prm = each[i];
+    m.npts = 1;
+    for (int d = 0; d < m.prm.ndim; ++d) m.npts *= m.prm.n[d];
+    m.slot_stride = m.npts / 2;
+    m.spec = plan_alloc(p, (size_t)(p->nf + 1) * m.slot_stride * cs);
+    m.real = plan_alloc(p, (size_t)p->nf * m.npts * rs);
+    int nx = m.prm.n[0], ny = m.prm.n[1], nz = m.prm.ndim > 2 ? m.prm.n[2] : 1;
+    m.k2x = (double*)plan_alloc(p, sizeof(double) * (nx + ny + nz + 2));
+    m.csum = (double*)plan_alloc(p, sizeof(double) * 8);
+    if (!m.spec || !m.real || !m.k2x || !m.csum) {
+      plan_free_all(p);
+      delete p;
+      return fail(nullptr, FS_ERR_OOM, "device workspace allocation failed");
+    }
+    m.k2y = m.k2x + nx;
+    m.k2z = m.k2y + ny;
+  }
+  p->tw = plan_alloc(p, (size_t)fs::kTwN * cs);
+  p->flag = (int*)plan_alloc(p, 256);
+  if (!p->tw || !p->flag) {
+    plan_free_all(p);
+    delete p;
+    return fail(nullptr, FS_ERR_OOM, "device workspace allocation failed");
+  }
+  cudaError_t e = cudaMallocHost(&p->host_flag, sizeof(int));
+  if (e != cudaSuccess) {
+    plan_free_all(p);
+    delete p;
+    return cuda_fail(nullptr, e, "cudaMallocHost");
+  }
+
+  // Twiddles exp(-2 pi i j / kTwN), long double on the host.
+  {
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<double> twd(2 * fs::kTwN);
+    for (int j = 0; j < fs::kTwN; ++j) {
+      long double ang = 2.0L * pi * (long double)j / (long double)fs::kTwN;
+      twd[2 * j] = (double)cosl(ang);
+      twd[2 * j + 1] = (double)(-sinl(ang));
+    }
+    if (p->f64) {
+      e = cudaMemcpy(p->tw, twd.data(), twd.size() * sizeof(double), cudaMemcpyHostToDevice);
+    } else {
+      std::vector<float> twf(twd.begin(), twd.end());
+      e = cudaMemcpy(p->tw, twf.data(), twf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+  }
+  for (Member& m : p->members) {
+    if (e != cudaSuccess) break;
+    int nx = m.prm.n[0], ny = m.prm.n[1], nz = m.prm.ndim > 2 ? m.prm.n[2] : 1;
+    std::vector<double> k2(nx + ny + nz + 2, 0.0);
+    for (int k = 0; k <= nx / 2; ++k) k2[k] = axis_k2(m.prm.lap, k, nx, m.prm.dx[0]);
+    for (int k = 0; k < ny; ++k) k2[nx + k] = axis_k2(m.prm.lap, k, ny, m.prm.dx[1]);
+    for (int k = 0; k < nz && m.prm.ndim > 2; ++k) k2[nx + ny + k] = axis_k2(m.prm.lap, k, nz, m.prm.dx[2]);
+    e = cudaMemcpy(m.k2x, k2.data(), k2.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m.csum, 0, sizeof(double) * 8);
+  }
+  if (e == cudaSuccess) e = cudaMemset(p->flag, 0, 256);
+  if (e != cudaSuccess) {
+    fs_status s = cuda_fail(nullptr, e, "plan tables");
+    cudaFreeHost(p->host_flag);
+    plan_free_all(p);
+    delete p;
+    return s;
+  }
+  *out = p;
+  return FS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fs_status fs_plan_create(const fs_params* prm, void* stream, fs_plan_t* out) {
+  return create_common(prm, 1, stream, nullptr, nullptr, nullptr, out);
+}
+
+fs_status fs_plan_create_ex(const fs_params* prm, void* stream, fs_alloc_fn alloc, fs_free_fn dealloc, void* ctx,
+                            fs_plan_t* out) {
+  return create_common(prm, 1, stream, alloc, dealloc, ctx, out);
+}
+
+fs_status fs_batch_create(const fs_params* each, int count, void* stream, fs_plan_t* out) {
+  return create_common(each, count, stream, nullptr, nullptr, nullptr, out);
+}
+
+fs_status fs_set_fields(fs_plan_t p, const void* const* fields) {
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  if (!fields) return fail(p, FS_ERR_INVALID_ARG, "fields is NULL");
+  const size_t rs = p->f64 ? sizeof(double) : sizeof(float);
+  int idx = 0;
+  for (Member& m : p->members) {
+    for (int f = 0; f < p->nf; ++f, ++idx) {
+      if (!fields[idx]) return fail(p, FS_ERR_INVALID_ARG, "field pointer is NULL");
+      char* dst = (char*)m.real + (size_t)f * m.npts * rs;
+      cudaError_t e = cudaMemcpyAsync(dst, fields[idx], m.npts * rs, cudaMemcpyDefault, p->stream);
+      if (e != cudaSuccess) return cuda_fail(p, e, "fs_set_fields copy");
+    }
+    if (!p->f64) {
+      cudaError_t e = cudaMemsetAsync(m.csum, 0, sizeof(double), p->stream);
+      if (e == cudaSuccess) e = fs::sum_launch_f32(m.real, m.npts, m.csum, p->stream);
+      if (e != cudaSuccess) return cuda_fail(p, e, "fs_set_fields mean carry");
+    }
+  }
+  p->state = kStateReal;
+  return FS_OK;
+}
+
+fs_status fs_step_async(fs_plan_t p, int64_t nsteps) {
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  if (nsteps < 0) return fail(p, FS_ERR_INVALID_ARG, "nsteps < 0");
+  if (p->state == kStateNone) return fail(p, FS_ERR_STATE, "fs_step before fs_set_fields");
+  int64_t launches = 0;
+  int64_t done = 0;
+  cudaError_t e = cudaSuccess;
+  if (nsteps > 0 && p->state == kStateReal) {
+    e = enqueue_step(p, 1, p->stream, &launches);
+    if (e != cudaSuccess) return cuda_fail(p, e, "step launch");
+    done = 1;
+    p->state = kStateSpec;
+  }
+  int64_t left = nsteps - done;
+  if (left >= kGraphSteps) {
+    if (!p->gexec) {
+      e = build_graph(p);
+      if (e != cudaSuccess) return cuda_fail(p, e, "graph capture");
+    }
+    while (left >= p->gsteps) {
+      e = cudaGraphLaunch(p->gexec, p->stream);
+      if (e != cudaSuccess) return cuda_fail(p, e, "graph launch");
+      left -= p->gsteps;
+      launches += (int64_t)p->gsteps * 2 * (int64_t)p->members.size();
+    }
+  }
+  for (; left > 0; --left) {
+    e = enqueue_step(p, 0, p->stream, &launches);
+    if (e != cudaSuccess) return cuda_fail(p, e, "step launch");
+  }
+  if (nsteps > 0) p->state = kStateSpec;
+  p->last_launches = launches;
+  return FS_OK;
+}
+
+fs_status fs_sync(fs_plan_t p) {
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  return read_flag(p);
+}
+
+fs_status fs_step(fs_plan_t p, int64_t nsteps) {
+  fs_status s = fs_step_async(p, nsteps);
+  if (s != FS_OK) return s;
+  return read_flag(p);
+}
+
+fs_status fs_get_fields(fs_plan_t p, void* const* out) {
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  if (!out) return fail(p, FS_ERR_INVALID_ARG, "fields_out is NULL");
+  if (p->state == kStateNone) return fail(p, FS_ERR_STATE, "fs_get_fields before fs_set_fields");
+  if (p->state == kStateSpec) {
+    for (const Member& m : p->members) {
+      fs::KArgs a = make_args(p, m, 2);
+      cudaError_t e = launch_row(p, a, p->stream);
+      if (e != cudaSuccess) return cuda_fail(p, e, "inverse row pass");
+    }
+    p->state = kStateReal;
+  }
+  const size_t rs = p->f64 ? sizeof(double) : sizeof(float);
+  int idx = 0;
+  for (const Member& m : p->members)
+    for (int f = 0; f < p->nf; ++f, ++idx) {
+      if (!out[idx]) return fail(p, FS_ERR_INVALID_ARG, "output pointer is NULL");
+      const char* src = (const char*)m.real + (size_t)f * m.npts * rs;
+      cudaError_t e = cudaMemcpyAsync(out[idx], src, m.npts * rs, cudaMemcpyDefault, p->stream);
+      if (e != cudaSuccess) return cuda_fail(p, e, "fs_get_fields copy");
+    }
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(p, e, "stream synchronize");
+  return FS_OK;
+}
+
+fs_status fs_set_params(fs_plan_t p, const fs_params* prm) {
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  if (p->members.size() != 1) return fail(p, FS_ERR_UNSUPPORTED, "fs_set_params on a batch plan");
+  std::string why;
+  fs_status s = validate(prm, &why);
+  if (s != FS_OK) return fail(p, s, why);
+  const fs_params& o = p->members[0].prm;
+  bool same = prm->ndim == o.ndim && prm->p == o.p && prm->precision == o.precision && prm->lap == o.lap &&
+              prm->scheme == o.scheme;
+  for (int d = 0; d < o.ndim; ++d) same = same && prm->n[d] == o.n[d] && prm->dx[d] == o.dx[d];
+  if (!same) return fail(p, FS_ERR_INVALID_ARG, "fs_set_params may change only physical parameters and dt");
+  p->members[0].prm = *prm;
+  drop_graph(p);
+  return FS_OK;
+}
+
+fs_status fs_set_stream(fs_plan_t p, void* stream) {
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  p->stream = reinterpret_cast<cudaStream_t>(stream);
+  return FS_OK;
+}
+
+fs_status fs_free_energy(fs_plan_t p, double* F, double* parts) {
+  (void)parts;
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  if (!F) return fail(p, FS_ERR_INVALID_ARG, "F is NULL");
+  return fail(p, FS_ERR_UNSUPPORTED, "fs_free_energy is not built in this library version");
+}
+
+fs_status fs_step_adjoint(fs_plan_t p, const void* const* u, const void* const* lam_in, void* const* lam_out,
+                          double grad[4]) {
+  (void)u;
+  (void)lam_in;
+  (void)lam_out;
+  (void)grad;
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  return fail(p, FS_ERR_UNSUPPORTED, "fs_step_adjoint is not built in this library version");
+}
+
+fs_status fs_step_profiled(fs_plan_t p, int64_t nsteps) {
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  if (nsteps < 0) return fail(p, FS_ERR_INVALID_ARG, "nsteps < 0");
+  if (p->state == kStateNone) return fail(p, FS_ERR_STATE, "fs_step before fs_set_fields");
+  cudaError_t e = cudaSuccess;
+  auto rec = [&](int k) {
+    if (e != cudaSuccess) return;
+    if (p->ev_used == p->ev_pool.size()) {
+      cudaEvent_t x;
+      e = cudaEventCreate(&x);
+      if (e != cudaSuccess) return;
+      p->ev_pool.push_back(x);
+      p->ev_kind.push_back(0);
+    }
+    p->ev_kind[p->ev_used] = k;
+    e = cudaEventRecord(p->ev_pool[p->ev_used], p->stream);
+    if (e == cudaSuccess) p->ev_used++;
+  };
+  int64_t launches = 0;
+  for (int64_t s = 0; s < nsteps && e == cudaSuccess; ++s) {
+    int mode = p->state == kStateReal ? 1 : 0;
+    for (const Member& m : p->members) {
+      fs::KArgs a = make_args(p, m, mode);
+      rec(0);
+      if (e == cudaSuccess) e = launch_row(p, a, p->stream);
+      rec(0);
+      rec(1);
+      if (e == cudaSuccess) e = launch_col(p, a, p->stream);
+      rec(1);
+      launches += 2;
+    }
+    p->state = kStateSpec;
+  }
+  if (e != cudaSuccess) return cuda_fail(p, e, "fs_step_profiled");
+  p->last_launches = launches;
+  return FS_OK;
+}
+
+fs_status fs_profile_read(fs_plan_t p, double* ms_per_pass, int64_t* launches_per_pass, int npass_max,
+                          int* npass) {
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  if (!ms_per_pass || !npass || npass_max < 1) return fail(p, FS_ERR_INVALID_ARG, "bad arguments");
+  const int kinds = 2;
+  double ms[kinds] = {0.0, 0.0};
+  int64_t cnt[kinds] = {0, 0};
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  for (size_t i = 0; e == cudaSuccess && i + 1 < p->ev_used; i += 2) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, p->ev_pool[i], p->ev_pool[i + 1]);
+    ms[p->ev_kind[i]] += t;
+    cnt[p->ev_kind[i]]++;
+  }
+  p->ev_used = 0;
+  if (e != cudaSuccess) return cuda_fail(p, e, "fs_profile_read");
+  int n = kinds < npass_max ? kinds : npass_max;
+  for (int i = 0; i < n; ++i) {
+    ms_per_pass[i] = ms[i];
+    if (launches_per_pass) launches_per_pass[i] = cnt[i];
+  }
+  *npass = n;
+  return read_flag(p);
+}
+
+fs_status fs_workspace_bytes(fs_plan_t p, size_t* bytes) {
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  if (!bytes) return fail(p, FS_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = p->ws_bytes;
+  return FS_OK;
+}
+
+fs_status fs_last_launch_count(fs_plan_t p, int64_t* launches) {
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  if (!launches) return fail(p, FS_ERR_INVALID_ARG, "launches is NULL");
+  *launches = p->last_launches;
+  return FS_OK;
+}
+
+fs_status fs_destroy(fs_plan_t p) {
+  if (!p) return FS_OK;
+  cudaStreamSynchronize(p->stream);
+  drop_graph(p);
+  for (cudaEvent_t x : p->ev_pool) cudaEventDestroy(x);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->host_flag) cudaFreeHost(p->host_flag);
+  plan_free_all(p);
+  delete p;
+  return FS_OK;
+}
+
+const char* fs_last_error(fs_plan_t p) { return p ? p->err.c_str() : g_thread_error.c_str(); }
+
+const char* fs_version(void) { return "fs-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"
