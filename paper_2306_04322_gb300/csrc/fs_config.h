@@ -1,0 +1,21 @@
+// Compile-time launch configuration shared by the kernels and the host-side
+// table builders (the host builds twiddle tables for exactly the (L, E) pairs
+// the kernels use).
+#pragma once
+
+namespace fs {
+
+// Complex values per thread of a row (x) line FFT of length L = nx / 2.
+constexpr int row_E(int L, bool f64) { return L < (f64 ? 8 : 16) ? L : (f64 ? 8 : 16); }
+// Complex values per thread of a column (y or z) line FFT of length L.
+constexpr int col_E(int L, bool f64) { return L < (f64 ? 8 : 16) ? L : (f64 ? 8 : 16); }
+// Threads per row-pass CTA (at least one row).
+constexpr int row_threads(int L, bool f64) {
+  return (L / row_E(L, f64)) > 128 ? (L / row_E(L, f64)) : 128;
+}
+// Columns per column-pass CTA: about 256 threads, at most 32 columns.
+constexpr int col_tk(int L, bool f64) {
+  return (256 / (L / col_E(L, f64))) < 1 ? 1 : ((256 / (L / col_E(L, f64))) > 32 ? 32 : (256 / (L / col_E(L, f64))));
+}
+
+}  // namespace fs

@@ -6,22 +6,21 @@
 // by TPL = L / E threads, each with E complex values in registers, thread t
 // holding elements t + TPL * m for m = 0..E-1 ("stride-TPL" order).  The FFT
 // is a Stockham autosort decomposition L = R_1 R_2 ... with every radix
-// R <= E; each pass does E/R radix-R butterflies per thread in registers.
-// Between passes the data goes through shared memory once; the last pass
-// leaves its results in the same stride-TPL order, so a line FFT of P passes
-// costs P - 1 shared-memory round trips and no global traffic.
+// R = min(E, remaining); each pass does E/R radix-R butterflies per thread in
+// registers.  Between passes the data goes through shared memory once; the
+// last pass leaves its results in the same stride-TPL order, so a line FFT of
+// P passes costs P - 1 shared-memory round trips and no global traffic.
 //
-// Twiddles come from one table tw[j] = exp(-2 pi i j / kTwN) built on the
-// host in long double; a root w_M^e is tw[(e mod M) * kTwN / M].  No device
-// trigonometry is used anywhere.
+// Twiddles: per-pass tables built on the host in long double, laid out
+// [pass][j][r] with r = 0..R-1 (entry r = 0 is 1), so a thread reads the
+// R - 1 twiddles of its butterfly as consecutive values.  No device
+// trigonometry is used.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace fs {
-
-constexpr int kTwN = 4096;  // master twiddle table length (max axis 2048)
 
 template <typename T> struct CplxOf;
 template <> struct CplxOf<float> { using type = float2; };
@@ -39,11 +38,19 @@ template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
   return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  return mk<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
 template <typename C> __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
 template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
 // multiply by +i (DIR = +1) or -i (DIR = -1)
 template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a) {
   return DIR > 0 ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);
+}
+// multiply by exp(DIR i theta) given w = exp(-i theta) (forward tables)
+template <int DIR, typename C> __device__ __forceinline__ C mul_tw(C a, C w) {
+  return DIR < 0 ? cmul(a, w) : cmulc(a, w);
 }
 
 constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
@@ -55,8 +62,7 @@ __host__ __device__ constexpr int bitrev(int v, int bits) {
   return r;
 }
 
-// cos / sin of 2 pi j / 32 for j = 0..8 (first octant and its end points),
-// decimal expansions of the exact values.
+// cos(2 pi j / 32) for j = 0..8, decimal expansions of the exact values.
 __device__ __forceinline__ double cos32(int j) {
   switch (j) {
     case 0: return 1.0;
@@ -72,7 +78,7 @@ __device__ __forceinline__ double cos32(int j) {
 }
 __device__ __forceinline__ double sin32(int j) { return cos32(8 - j); }
 
-// Multiply a by exp(DIR * 2 pi i * k / len) for a compile-time-known k/len
+// Multiply a by exp(DIR * 2 pi i * k / len) for compile-time-known k / len
 // (after unrolling), len <= 32.  Trivial roots avoid multiplies.
 template <int DIR, typename C>
 __device__ __forceinline__ C twiddle_small(C a, int k, int len) {
@@ -82,28 +88,23 @@ __device__ __forceinline__ C twiddle_small(C a, int k, int len) {
   if (j == 8) return mul_i<DIR>(a);
   if (j == 16) return mk<C>(-a.x, -a.y);
   if (j == 24) return mul_i<-DIR>(a);
-  // reduce to first quadrant: exp(i theta), theta = 2 pi j / 32
   int q = j / 8, r = j % 8;
   T c = (T)cos32(r), s = (T)sin32(r);
-  // rotate by q quarter turns
   T cr, sr;
   if (q == 0) { cr = c; sr = s; }
   else if (q == 1) { cr = -s; sr = c; }
   else if (q == 2) { cr = -c; sr = -s; }
   else { cr = s; sr = -c; }
-  if (r == 4) {  // (+-1 +- i)/sqrt(2): 2 adds + 2 multiplies
+  if (r == 4) {  // (+-1 +- i)/sqrt(2): adds, then one scaling
     T h = (T)cos32(4);
     T sx = (cr > 0 ? 1 : -1), sy = (DIR * sr > 0 ? 1 : -1);
-    // (a.x + i a.y)(sx + i sy) h
     return mk<C>((sx * a.x - sy * a.y) * h, (sy * a.x + sx * a.y) * h);
   }
-  C w = mk<C>(cr, DIR * sr);
-  return cmul(a, w);
+  return cmul(a, mk<C>(cr, DIR * sr));
 }
 
 // In-register DFT of length R (R <= 32) on a[0], a[S], ..., a[(R-1) S],
 // natural order in and out, X[k] = sum_n x[n] exp(DIR 2 pi i n k / R).
-// Radix-2 decimation in time with a compile-time bit reversal.
 template <int R, int DIR, int S, typename C>
 __device__ __forceinline__ void reg_dft(C* a) {
   if constexpr (R == 1) {
@@ -124,13 +125,10 @@ __device__ __forceinline__ void reg_dft(C* a) {
     C t[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) t[i] = a[bitrev(i, B) * S];
-    // first two levels as radix-4 butterflies on bit-reversed data
 #pragma unroll
     for (int i = 0; i < R; i += 4) {
       C x0 = t[i], x1 = t[i + 1], x2 = t[i + 2], x3 = t[i + 3];
-      // length-2 DFTs: (x0,x1), (x2,x3); then length-4 combine
-      C a0 = cadd(x0, x1), a1 = csub(x0, x1), b0 = cadd(x2, x3), b1 = csub(x2, x3);
-      b1 = mul_i<DIR>(b1);
+      C a0 = cadd(x0, x1), a1 = csub(x0, x1), b0 = cadd(x2, x3), b1 = mul_i<DIR>(csub(x2, x3));
       t[i] = cadd(a0, b0);
       t[i + 2] = csub(a0, b0);
       t[i + 1] = cadd(a1, b1);
@@ -154,26 +152,39 @@ __device__ __forceinline__ void reg_dft(C* a) {
   }
 }
 
-// Twiddle exp(DIR * 2 pi i * e / M) from the master table.
-template <int DIR, int M, typename C>
-__device__ __forceinline__ C tw_root(const C* __restrict__ tw, int e) {
-  C w = __ldg(&tw[(e & (M - 1)) * (kTwN / M)]);
-  if (DIR > 0) w.y = -w.y;
-  return w;
-}
-
-// Radix sequence: each pass uses R = min(E, remaining).
+// ---- pass structure (identical on host and device) -------------------------
 template <int L, int E, int NS>
 struct PassRadix {
   static constexpr int R = imin(E, L / NS);
 };
+// offset (in complex entries) of the table of the pass starting at NS
+template <int L, int E, int NS>
+constexpr int pass_table_offset() {
+  int off = 0;
+  for (int ns = 1; ns < NS;) {
+    int r = imin(E, L / ns);
+    if (ns > 1) off += ns * r;
+    ns *= r;
+  }
+  return off;
+}
+// total table size of a line FFT of length L with E per thread
+__host__ __device__ constexpr int pass_table_size(int L, int E) {
+  int off = 0;
+  for (int ns = 1; ns < L;) {
+    int r = E < L / ns ? E : L / ns;
+    if (ns > 1) off += ns * r;
+    ns *= r;
+  }
+  return off;
+}
 
 // One Stockham pass (and, recursively, the following ones).  On entry the
 // thread holds pass inputs x[b + r L/R] for its butterflies b = t + TPL q in
 // v[q + (E/R) r].  Not-last passes write outputs to shared memory through
 // `st` and read the next pass's inputs back in stride-TPL order.
 template <int L, int E, int NS, int DIR, typename C, class Store, class Load, class Sync>
-__device__ __forceinline__ void stockham(C (&v)[E], int t, const C* __restrict__ tw, Store st, Load ld,
+__device__ __forceinline__ void stockham(C (&v)[E], int t, const C* __restrict__ twp, Store st, Load ld,
                                          Sync sync) {
   constexpr int TPL = L / E;
   constexpr int R = PassRadix<L, E, NS>::R;
@@ -181,11 +192,12 @@ __device__ __forceinline__ void stockham(C (&v)[E], int t, const C* __restrict__
   static_assert(E % R == 0, "radix must divide E");
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    int b = t + TPL * q;
+    const int b = t + TPL * q;
     if constexpr (NS > 1) {
-      int j = b & (NS - 1);
+      const int j = b & (NS - 1);
+      const C* w = twp + pass_table_offset<L, E, NS>() + j * R;
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[q + Q * r] = cmul(v[q + Q * r], tw_root<DIR, NS * R>(tw, r * j));
+      for (int r = 1; r < R; ++r) v[q + Q * r] = mul_tw<DIR>(v[q + Q * r], __ldg(&w[r]));
     }
     reg_dft<R, DIR, Q>(&v[q]);
   }
@@ -193,30 +205,70 @@ __device__ __forceinline__ void stockham(C (&v)[E], int t, const C* __restrict__
     sync();
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      int b = t + TPL * q;
-      int j = b & (NS - 1);
-      int base = (b - j) * R + j;
+      const int b = t + TPL * q;
+      const int j = b & (NS - 1);
+      const int base = (b - j) * R + j;
 #pragma unroll
       for (int r = 0; r < R; ++r) st(base + r * NS, v[q + Q * r]);
     }
     sync();
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = ld(t + TPL * m);
-    stockham<L, E, NS * R, DIR>(v, t, tw, st, ld, sync);
+    stockham<L, E, NS * R, DIR>(v, t, twp, st, ld, sync);
   }
 }
 
 // Full line FFT, X[k] = sum_n x[n] exp(DIR 2 pi i n k / L), unnormalised.
+// twp: the pass tables of (L, E) (forward roots; the inverse conjugates).
 template <int L, int E, int DIR, typename C, class Store, class Load, class Sync>
-__device__ __forceinline__ void line_fft(C (&v)[E], int t, const C* __restrict__ tw, Store st, Load ld,
+__device__ __forceinline__ void line_fft(C (&v)[E], int t, const C* __restrict__ twp, Store st, Load ld,
                                          Sync sync) {
   static_assert(L % E == 0, "E must divide L");
-  stockham<L, E, 1, DIR>(v, t, tw, st, ld, sync);
+  stockham<L, E, 1, DIR>(v, t, twp, st, ld, sync);
 }
 
 // Padded shared-memory index: one spare slot every 32 elements keeps the
 // stride-R butterfly writes and the stride-TPL reads free of bank conflicts.
 __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 constexpr int padded_len(int L) { return L + L / 32 + 1; }
+
+// ---- asynchronous bulk copies and mbarriers (inline PTX, sm_90+) ----------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// Global -> shared bulk copy (bytes a multiple of 16, both addresses 16-byte
+// aligned), completion signalled on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: true when the phase completed, false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
 
 }  // namespace fs

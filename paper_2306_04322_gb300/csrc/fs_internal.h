@@ -5,18 +5,27 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fs_config.h"
+
 namespace fs {
 
 enum : int { FS_FLAG_NONFINITE = 1, FS_FLAG_TIMEOUT = 2, FS_FLAG_BOUNDS = 4 };
 
-// Arguments of one pass over one simulation (passed by value).
+// Polls of an mbarrier before a wait gives up and reports FS_FLAG_TIMEOUT.
+constexpr uint32_t kWaitPolls = 1u << 20;
+
+// Arguments of one pass over one simulation (passed by value).  Array
+// pointers are in the plan's precision T (float or double) unless noted.
 struct KArgs {
   void* spec;              // packed half spectra: slots of slot_stride complex values
   void* real;              // real fields: nf arrays of npts values
-  const void* tw;          // master twiddle table (complex, plan precision)
-  const double* k2x;       // |xi_x|^2 per x bin, nx/2 + 1 entries
-  const double* k2y;       // |xi_y|^2 per y bin, ny entries
-  const double* k2z;       // |xi_z|^2 per z bin, nz entries (3D)
+  const void* tw_row;      // pass tables of the x line FFT (L = nx/2)
+  const void* tw_col;      // pass tables of the y line FFT (L = ny)
+  const void* tw_z;        // pass tables of the z line FFT (L = nz, 3D)
+  const void* tw_half;     // exp(-2 pi i k / nx), k = 0..nx/2-1 (real <-> half-length complex)
+  const void* k2x;         // |xi_x|^2 per x bin, nx/2 + 1 entries
+  const void* k2y;         // |xi_y|^2 per y bin, ny entries
+  const void* k2z;         // |xi_z|^2 per z bin, nz entries (3D)
   long long slot_stride;   // complex values per spectrum slot
   long long npts;          // real points per field
   int nx, ny, nz, nf;

@@ -23,7 +23,7 @@ cudaError_t row_launch_n(const KArgs& a, cudaStream_t s) {
   using Cfg = RowCfg<T, NX>;
   long long rpc = Cfg::THREADS / Cfg::TPL;
   if (rpc > a.lines) rpc = a.lines;
-  size_t smem = (size_t)rpc * (a.nf + 1) * Cfg::PL * sizeof(cplx<T>);
+  size_t smem = Cfg::BAR_BYTES + (size_t)rpc * a.nf * Cfg::PL * sizeof(cplx<T>);
   static unsigned done = 0;
   cudaError_t e = allow_big_smem(fs_row_kernel<T, NX>, &done);
   if (e != cudaSuccess) return e;
@@ -36,11 +36,12 @@ cudaError_t col_launch_n(const KArgs& a, cudaStream_t s) {
   using Cfg = ColCfg<T, NY>;
   int Lh = a.nx / 2;
   int tk = Cfg::TK < Lh ? Cfg::TK : Lh;
-  size_t smem = (size_t)NY * tk * sizeof(cplx<T>);
+  size_t smem = 2 * (size_t)NY * tk * sizeof(cplx<T>);
   static unsigned done = 0;
   cudaError_t e = allow_big_smem(fs_col_kernel<T, NY>, &done);
   if (e != cudaSuccess) return e;
-  fs_col_kernel<T, NY><<<(unsigned)(Lh / tk), (unsigned)(tk * Cfg::TPL), smem, s>>>(a);
+  dim3 grid((unsigned)(Lh / tk), (unsigned)a.nf);
+  fs_col_kernel<T, NY><<<grid, (unsigned)(tk * Cfg::TPL), smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -14,15 +14,16 @@
 // Pass structure on the device (2D, nf = 1 + p fields, all spectra stored as
 // packed half spectra along x: nx/2 complex per row, bin 0 holding the real
 // DC value in .x and the real Nyquist value in .y):
-//   row pass    (one CTA per group of rows): inverse x transform of the
-//               previous step's spectra (or a load of the real fields), the
+//   row pass    (one group of threads per row): bulk-async load of every
+//               field's row into shared memory, inverse x transform of the
+//               previous step's spectra (or the real fields as loaded), the
 //               pointwise derivative stage, and forward x transforms of
 //               c, g_i = eta_i - L dt df/deta_i and df/dc.  Linearity of the
 //               DFT lets the eta update use one transform of g_i instead of
 //               two (eta^ - L dt (df/deta)^ = (eta - L dt df/deta)^).
-//   column pass (one CTA per tile of kx columns): forward y transforms, the
-//               per-mode k-space update with the 1/N scale folded in, and
-//               inverse y transforms, in place.
+//   column pass (one CTA per tile of kx columns and per field group): forward
+//               y transforms, the per-mode k-space update with the 1/N scale
+//               folded in, and inverse y transforms, in place.
 // The next step's row pass starts with the inverse x transform, so the real
 // fields only reach global memory when they are asked for.
 #pragma once
@@ -66,8 +67,10 @@ __device__ __forceinline__ bool finite_val(T x) {
 }
 
 // ---------------------------------------------------------------------------
-// Row pass.  Lines along x; one group of TPL threads per row.
-// Shared memory per row: (nf + 1) slots of padded_len(L) complex values.
+// Row pass.  Lines along x; TPL threads per row, rpc rows per CTA.
+// Shared memory: rpc mbarriers, then per row nf slots of PL complex values.
+// Slot contents use the natural layout (element i at i) except during the
+// FFT exchanges, which use the padded layout (element i at pad32(i)).
 // mode 0: step, previous state in spec slots 0..nf-1 (y-inverted spectra)
 // mode 1: step, previous state in the real fields
 // mode 2: inverse only: spec slots 0..nf-1 -> real fields
@@ -77,11 +80,13 @@ __device__ __forceinline__ bool finite_val(T x) {
 // ---------------------------------------------------------------------------
 template <typename T, int NX>
 struct RowCfg {
+  static constexpr bool F64 = sizeof(T) == 8;
   static constexpr int L = NX / 2;
-  static constexpr int E = imin(L, sizeof(T) == 4 ? 16 : 8);
+  static constexpr int E = row_E(L, F64);
   static constexpr int TPL = L / E;
-  static constexpr int PL = padded_len(L);
-  static constexpr int THREADS = imax(TPL, 128);
+  static constexpr int PL = (padded_len(L) + 1) & ~1;  // even: 16-byte aligned slots
+  static constexpr int THREADS = row_threads(L, F64);
+  static constexpr int BAR_BYTES = 1024;  // room for the mbarriers of up to 128 rows
 };
 
 template <typename T, int NX>
@@ -89,110 +94,137 @@ __global__ void __launch_bounds__(RowCfg<T, NX>::THREADS) fs_row_kernel(KArgs a)
   using C = cplx<T>;
   using Cfg = RowCfg<T, NX>;
   constexpr int L = Cfg::L, E = Cfg::E, TPL = Cfg::TPL, PL = Cfg::PL;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
   const int nf = a.nf;
   const int rl = threadIdx.x / TPL, t = threadIdx.x % TPL;
   const int rpc = blockDim.x / TPL;
   const long long row = (long long)blockIdx.x * rpc + rl;
-  C* slots = sm + (size_t)rl * (nf + 1) * PL;
-  const C* __restrict__ tw = reinterpret_cast<const C*>(a.tw);
+  C* slots = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES) + (size_t)rl * nf * PL;
+  const C* __restrict__ twr = reinterpret_cast<const C*>(a.tw_row);
+  const C* __restrict__ twh = reinterpret_cast<const C*>(a.tw_half);
   C* spec = reinterpret_cast<C*>(a.spec);
   C* realc = reinterpret_cast<C*>(a.real);  // real row as complex pairs
   const long long half_stride = a.npts / 2;  // complex pairs per real field
-  auto sync = []() { __syncthreads(); };
+  auto sync = []() {
+    if constexpr (TPL == 32) __syncwarp(); else __syncthreads();
+  };
 
-  bool bad = false;
-  // 1. real-space row of every field into its slot (as pairs x[2j], x[2j+1])
-  for (int f = 0; f < nf; ++f) {
-    C* s = slots + f * PL;
-    auto st = [s](int i, C v) { s[pad32(i)] = v; };
-    auto ld = [s](int i) { return s[pad32(i)]; };
-    C v[E];
-    if (a.mode == 1) {
-      const C* src = realc + f * half_stride + row * L;
-#pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = src[t + TPL * m];
-    } else {
-      const C* P = spec + f * a.slot_stride + row * L;
+  // 1. bulk-async load of every field's row (spectra or real pairs)
+  uint64_t* bar = bars + rl;
+  if (t == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (t == 0) {
+    const uint32_t bytes = (uint32_t)(L * sizeof(C));
+    mbar_arrive_expect_tx(bar, bytes * nf);
+    for (int f = 0; f < nf; ++f) {
+      const C* src = (a.mode == 1) ? realc + f * half_stride + row * L : spec + f * a.slot_stride + row * L;
+      bulk_g2s(slots + f * PL, src, bytes, bar);
+    }
+  }
+  if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
+    if (t == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
+    mbar_wait_bounded(bar, 0, kWaitPolls);  // let the copies land before exiting
+    return;
+  }
+
+  // 2. inverse x transforms (real pairs x[2j], x[2j+1] back into the slots)
+  if (a.mode != 1) {
+    for (int f = 0; f < nf; ++f) {
+      C* s = slots + f * PL;
+      auto st = [s](int i, C v) { s[pad32(i)] = v; };
+      auto ld = [s](int i) { return s[pad32(i)]; };
+      C v[E];
 #pragma unroll
       for (int m = 0; m < E; ++m) {
-        int k = t + TPL * m;
-        C pk = P[k];
+        const int k = t + TPL * m;
+        const C pk = s[k];
         if (k == 0) {
           v[m] = mk<C>(pk.x + pk.y, pk.x - pk.y);
         } else {
-          C pm = P[L - k];
-          C A = cadd(pk, cconj(pm)), B = csub(pk, cconj(pm));
-          v[m] = cadd(A, mul_i<1>(cmul(tw_root<1, NX>(tw, k), B)));
+          const C pm = cconj(s[L - k]);
+          const C A = cadd(pk, pm), B = csub(pk, pm);
+          v[m] = cadd(A, mul_i<1>(mul_tw<1>(B, __ldg(&twh[k]))));
         }
       }
-      line_fft<L, E, 1>(v, t, tw, st, ld, sync);
-      sync();
-    }
-    if (a.mode == 2) {
-      C* dst = realc + f * half_stride + row * L;
+      line_fft<L, E, 1>(v, t, twr, st, ld, sync);
+      if (a.mode == 2) {
+        C* dst = realc + f * half_stride + row * L;
 #pragma unroll
-      for (int m = 0; m < E; ++m) dst[t + TPL * m] = v[m];
-    } else {
+        for (int m = 0; m < E; ++m) dst[t + TPL * m] = v[m];
+      } else {
+        sync();
 #pragma unroll
-      for (int m = 0; m < E; ++m) st(t + TPL * m, v[m]);
+        for (int m = 0; m < E; ++m) s[t + TPL * m] = v[m];
+      }
     }
+    if (a.mode == 2) return;
   }
-  if (a.mode == 2) return;
 
-  // 2. pointwise derivative stage on the thread's own points
+  // 3. pointwise derivative stage on the thread's own points:
+  //    df/dc kept in registers, g_i written over eta_i
+  C fcv[E];
+  bool bad = false;
   {
-    Pointwise<T> pw(a);
+    const Pointwise<T> pw(a);
     const int p = nf - 1;
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-      const int ip = pad32(t + TPL * m);
-      C c = slots[ip];
+      const int i0 = t + TPL * m;
+      const C c = slots[i0];
       C h = mk<C>(T(0), T(0)), S2 = mk<C>(T(0), T(0));
+      bad |= !(finite_val(c.x) && finite_val(c.y));
       for (int i = 0; i < p; ++i) {
-        C e = slots[(1 + i) * PL + ip];
+        const C e = slots[(1 + i) * PL + i0];
         h.x += pw.hpoly(e.x);
         h.y += pw.hpoly(e.y);
         S2.x += e.x * e.x;
         S2.y += e.y * e.y;
         bad |= !(finite_val(e.x) && finite_val(e.y));
       }
-      bad |= !(finite_val(c.x) && finite_val(c.y));
-      slots[nf * PL + ip] = mk<C>(pw.fc(c.x, h.x), pw.fc(c.y, h.y));
+      fcv[m] = mk<C>(pw.fc(c.x, h.x), pw.fc(c.y, h.y));
       for (int i = 0; i < p; ++i) {
-        C e = slots[(1 + i) * PL + ip];
-        C g = mk<C>(e.x - pw.Ldt * pw.feta(c.x, e.x, S2.x), e.y - pw.Ldt * pw.feta(c.y, e.y, S2.y));
-        slots[(1 + i) * PL + ip] = g;
+        const C e = slots[(1 + i) * PL + i0];
+        slots[(1 + i) * PL + i0] =
+            mk<C>(e.x - pw.Ldt * pw.feta(c.x, e.x, S2.x), e.y - pw.Ldt * pw.feta(c.y, e.y, S2.y));
       }
     }
   }
 
-  // 3. forward x transforms (packed half spectra, scaled by 2)
+  // 4. forward x transforms of c, g_1..g_p (slots) and df/dc (registers),
+  //    packed half spectra scaled by 2, straight to global memory
   for (int o = 0; o <= nf; ++o) {
-    C* s = slots + o * PL;
+    C* s = slots + (o < nf ? o : 0) * PL;
     auto st = [s](int i, C v) { s[pad32(i)] = v; };
     auto ld = [s](int i) { return s[pad32(i)]; };
     C v[E];
+    if (o < nf) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = ld(t + TPL * m);
-    line_fft<L, E, -1>(v, t, tw, st, ld, sync);
+      for (int m = 0; m < E; ++m) v[m] = s[t + TPL * m];
+    } else {
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = fcv[m];
+    }
+    line_fft<L, E, -1>(v, t, twr, st, ld, sync);
     sync();
 #pragma unroll
-    for (int m = 0; m < E; ++m) st(t + TPL * m, v[m]);
+    for (int m = 0; m < E; ++m) s[t + TPL * m] = v[m];
     sync();
     C* P = spec + o * a.slot_stride + row * L;
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-      int k = t + TPL * m;
-      C zk = ld(k);
+      const int k = t + TPL * m;
+      const C zk = s[k];
       C out;
       if (k == 0) {
         out = mk<C>(T(2) * (zk.x + zk.y), T(2) * (zk.x - zk.y));
       } else {
-        C zm = ld(L - k);
-        C A = cadd(zk, cconj(zm)), B = csub(zk, cconj(zm));
-        out = cadd(A, mul_i<-1>(cmul(tw_root<-1, NX>(tw, k), B)));
+        const C zm = cconj(s[L - k]);
+        const C A = cadd(zk, zm), B = csub(zk, zm);
+        out = cadd(A, mul_i<-1>(cmul(B, __ldg(&twh[k]))));
       }
       P[k] = out;
     }
@@ -202,14 +234,18 @@ __global__ void __launch_bounds__(RowCfg<T, NX>::THREADS) fs_row_kernel(KArgs a)
 
 // ---------------------------------------------------------------------------
 // Column pass (2D step).  Lines along y of the packed x-spectra; one CTA per
-// tile of TK adjacent kx columns, TPL threads per column.  Forward y
-// transforms, k-space update, inverse y transforms, in place.
+// tile of tk adjacent kx columns (TPL threads per column) and per field group
+// (blockIdx.y = 0: c with df/dc, g >= 1: eta_g).  Forward y transforms,
+// k-space update, inverse y transforms, in place.
+// Shared memory: exchange tile [NY][tk] and, for the c group, the forward
+// transform of df/dc [NY][tk].
 // ---------------------------------------------------------------------------
 template <typename T, int NY>
 struct ColCfg {
-  static constexpr int E = imin(NY, sizeof(T) == 4 ? 16 : 8);
+  static constexpr bool F64 = sizeof(T) == 8;
+  static constexpr int E = col_E(NY, F64);
   static constexpr int TPL = NY / E;
-  static constexpr int TK = imin(sizeof(T) == 4 ? 16 : 8, imax(1, 512 / TPL));
+  static constexpr int TK = col_tk(NY, F64);
   static constexpr int THREADS = TPL * TK;
 };
 
@@ -234,125 +270,92 @@ struct KUpdate {
 };
 
 template <typename T, int NY>
-__global__ void __launch_bounds__(ColCfg<T, NY>::THREADS) fs_col_kernel(KArgs a) {
+__global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2) fs_col_kernel(KArgs a) {
   using C = cplx<T>;
   using Cfg = ColCfg<T, NY>;
   constexpr int E = Cfg::E, TPL = Cfg::TPL;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tile = reinterpret_cast<C*>(smem_raw);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int tk = blockDim.x / TPL;  // columns in this CTA (<= TK)
+  C* tile = reinterpret_cast<C*>(smem_raw);
+  C* stash = tile + NY * tk;
   const int j = threadIdx.x % tk, t = threadIdx.x / tk;
   const int Lh = a.nx / 2;
   const int kx0 = blockIdx.x * tk;
   const int kx = kx0 + j;
-  const C* __restrict__ tw = reinterpret_cast<const C*>(a.tw);
-  C* spec = reinterpret_cast<C*>(a.spec) + kx;
+  const int g = blockIdx.y;  // field group
+  const int nf = a.nf;
+  const C* __restrict__ twc = reinterpret_cast<const C*>(a.tw_col);
+  const T* __restrict__ k2xt = reinterpret_cast<const T*>(a.k2x);
+  const T* __restrict__ k2yt = reinterpret_cast<const T*>(a.k2y);
+  C* base = reinterpret_cast<C*>(a.spec) + kx;
   auto st = [tile, tk, j](int i, C v) { tile[i * tk + j] = v; };
   auto ld = [tile, tk, j](int i) { return tile[i * tk + j]; };
   auto sync = []() { __syncthreads(); };
   const KUpdate<T> up(a);
-  const int nf = a.nf;
   const bool special = (kx0 == 0);  // CTA holding the packed DC/Nyquist column
-  const T kx2 = (T)__ldg(&a.k2x[kx]);
-  const T kxn2 = (T)__ldg(&a.k2x[Lh]);  // Nyquist column
+  const T kx2 = k2xt[kx];
+  const T kxn2 = k2xt[Lh];  // Nyquist column
 
-  // ---- c and df/dc
-  C vc[E], vf[E];
-  {
-    const C* Sc = spec;
-    const C* Sf = spec + (long long)nf * a.slot_stride;
+  // forward transforms: c group takes df/dc (slot nf, kept in `stash`) then c
+  const int nin = (g == 0) ? 2 : 1;
+  C v[E];
+  for (int i = 0; i < nin; ++i) {
+    const int slot = (g == 0) ? (i == 0 ? nf : 0) : g;
+    const C* S = base + (long long)slot * a.slot_stride;
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      vc[m] = Sc[(long long)(t + TPL * m) * Lh];
-      vf[m] = Sf[(long long)(t + TPL * m) * Lh];
+    for (int m = 0; m < E; ++m) v[m] = S[(long long)(t + TPL * m) * Lh];
+    line_fft<NY, E, -1>(v, t, twc, st, ld, sync);
+    if (g == 0 && i == 0) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) stash[(t + TPL * m) * tk + j] = v[m];
     }
   }
-  line_fft<NY, E, -1>(vc, t, tw, st, ld, sync);
-  line_fft<NY, E, -1>(vf, t, tw, st, ld, sync);
+
   if (special) {
     // Separate the packed column Z = A + i B (A: kx = 0, B: kx = nx/2, both
     // Hermitian in ky) through shared memory, update both, repack.
     sync();
-    C* zc = tile;
-    C* zf = tile + NY;
     if (j == 0) {
 #pragma unroll
-      for (int m = 0; m < E; ++m) {
-        zc[t + TPL * m] = vc[m];
-        zf[t + TPL * m] = vf[m];
-      }
+      for (int m = 0; m < E; ++m) tile[(t + TPL * m) * tk] = v[m];
     }
     sync();
-    if (j == 0) {
+  }
+  if (special && j == 0) {
 #pragma unroll
-      for (int m = 0; m < E; ++m) {
-        int ky = t + TPL * m, kq = (NY - ky) & (NY - 1);
-        C pc = cconj(zc[kq]), pf = cconj(zf[kq]);
-        C Ac = cscale(cadd(vc[m], pc), T(0.5)), Bc = cscale(mul_i<-1>(csub(vc[m], pc)), T(0.5));
-        C Af = cscale(cadd(vf[m], pf), T(0.5)), Bf = cscale(mul_i<-1>(csub(vf[m], pf)), T(0.5));
-        T ky2 = (T)__ldg(&a.k2y[ky]);
-        C An = up.c(Ac, Af, kx2 + ky2);
-        C Bn = up.c(Bc, Bf, kxn2 + ky2);
+    for (int m = 0; m < E; ++m) {
+      const int ky = t + TPL * m, kq = (NY - ky) & (NY - 1);
+      const T ky2 = k2yt[ky];
+      const C pz = cconj(tile[kq * tk]);
+      const C A = cscale(cadd(v[m], pz), T(0.5)), B = cscale(mul_i<-1>(csub(v[m], pz)), T(0.5));
+      C An, Bn;
+      if (g == 0) {
+        const C zf = stash[ky * tk], pf = cconj(stash[kq * tk]);
+        const C Af = cscale(cadd(zf, pf), T(0.5)), Bf = cscale(mul_i<-1>(csub(zf, pf)), T(0.5));
+        An = up.c(A, Af, kx2 + ky2);
+        Bn = up.c(B, Bf, kxn2 + ky2);
         if (ky == 0 && a.csum) An = mk<C>((T)(*a.csum * a.inv_npts), T(0));
-        vc[m] = cadd(An, mul_i<1>(Bn));
+      } else {
+        An = up.eta(A, kx2 + ky2);
+        Bn = up.eta(B, kxn2 + ky2);
       }
-    } else {
+      v[m] = cadd(An, mul_i<1>(Bn));
+    }
+  } else if (g == 0) {
 #pragma unroll
-      for (int m = 0; m < E; ++m) {
-        int ky = t + TPL * m;
-        vc[m] = up.c(vc[m], vf[m], kx2 + (T)__ldg(&a.k2y[ky]));
-      }
+    for (int m = 0; m < E; ++m) {
+      const int ky = t + TPL * m;
+      v[m] = up.c(v[m], stash[ky * tk + j], kx2 + k2yt[ky]);
     }
   } else {
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      int ky = t + TPL * m;
-      vc[m] = up.c(vc[m], vf[m], kx2 + (T)__ldg(&a.k2y[ky]));
-    }
-  }
-  line_fft<NY, E, 1>(vc, t, tw, st, ld, sync);
-  {
-    C* Sc = spec;
-#pragma unroll
-    for (int m = 0; m < E; ++m) Sc[(long long)(t + TPL * m) * Lh] = vc[m];
+    for (int m = 0; m < E; ++m) v[m] = up.eta(v[m], kx2 + k2yt[t + TPL * m]);
   }
 
-  // ---- eta_i (slot i holds g_i = eta_i - L dt df/deta_i)
-  for (int i = 1; i < nf; ++i) {
-    C* S = spec + (long long)i * a.slot_stride;
-    C v[E];
+  line_fft<NY, E, 1>(v, t, twc, st, ld, sync);
+  C* S = base + (long long)(g == 0 ? 0 : g) * a.slot_stride;
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = S[(long long)(t + TPL * m) * Lh];
-    line_fft<NY, E, -1>(v, t, tw, st, ld, sync);
-    if (special) {
-      sync();
-      C* z = tile;
-      if (j == 0) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) z[t + TPL * m] = v[m];
-      }
-      sync();
-      if (j == 0) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-          int ky = t + TPL * m, kq = (NY - ky) & (NY - 1);
-          C pz = cconj(z[kq]);
-          C A = cscale(cadd(v[m], pz), T(0.5)), B = cscale(mul_i<-1>(csub(v[m], pz)), T(0.5));
-          T ky2 = (T)__ldg(&a.k2y[ky]);
-          v[m] = cadd(up.eta(A, kx2 + ky2), mul_i<1>(up.eta(B, kxn2 + ky2)));
-        }
-      } else {
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = up.eta(v[m], kx2 + (T)__ldg(&a.k2y[t + TPL * m]));
-      }
-    } else {
-#pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = up.eta(v[m], kx2 + (T)__ldg(&a.k2y[t + TPL * m]));
-    }
-    line_fft<NY, E, 1>(v, t, tw, st, ld, sync);
-#pragma unroll
-    for (int m = 0; m < E; ++m) S[(long long)(t + TPL * m) * Lh] = v[m];
-  }
+  for (int m = 0; m < E; ++m) S[(long long)(t + TPL * m) * Lh] = v[m];
 }
 
 }  // namespace fs

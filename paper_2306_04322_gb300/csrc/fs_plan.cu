@@ -26,9 +26,13 @@ struct Member {
   // device pointers into the plan's arena
   void* spec = nullptr;
   void* real = nullptr;
-  double* k2x = nullptr;
-  double* k2y = nullptr;
-  double* k2z = nullptr;
+  void* k2x = nullptr;  // plan precision
+  void* k2y = nullptr;
+  void* k2z = nullptr;
+  void* tw_row = nullptr;  // complex, plan precision
+  void* tw_col = nullptr;
+  void* tw_z = nullptr;
+  void* tw_half = nullptr;
   double* csum = nullptr;
   long long slot_stride = 0;
 };
@@ -46,7 +50,6 @@ struct fs_plan {
   void* actx = nullptr;
   std::vector<void*> blocks;
   size_t ws_bytes = 0;
-  void* tw = nullptr;
   int* flag = nullptr;
   int* host_flag = nullptr;  // pinned
   int state = kStateNone;
@@ -191,7 +194,10 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   std::memset(&a, 0, sizeof(a));
   a.spec = m.spec;
   a.real = m.real;
-  a.tw = p->tw;
+  a.tw_row = m.tw_row;
+  a.tw_col = m.tw_col;
+  a.tw_z = m.tw_z;
+  a.tw_half = m.tw_half;
   a.k2x = m.k2x;
   a.k2y = m.k2y;
   a.k2z = m.k2z;
@@ -287,6 +293,129 @@ fs_status read_flag(fs_plan* p) {
   return FS_OK;
 }
 
+// ---- per-member constant tables --------------------------------------------
+// Layout of one member's table block (plan precision T, complex = 2 T):
+//   k2x[nx/2 + 1] | k2y[ny] | k2z[nz]        (real, padded to 16 bytes)
+//   tw_row | tw_col | tw_z                  (Stockham pass tables, complex)
+//   tw_half[nx/2]                           (exp(-2 pi i k / nx), complex)
+struct TableLayout {
+  size_t k2x, k2y, k2z, tw_row, tw_col, tw_z, tw_half, total;  // offsets in bytes
+  int Lrow, Erow, Lcol, Ecol, Lz, Ez;
+};
+
+size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+TableLayout table_layout(const fs_params& prm, bool f64) {
+  TableLayout t{};
+  const size_t rs = f64 ? 8 : 4, cs = 2 * rs;
+  int nx = prm.n[0], ny = prm.n[1], nz = prm.ndim > 2 ? prm.n[2] : 1;
+  t.Lrow = nx / 2;
+  t.Erow = fs::row_E(t.Lrow, f64);
+  t.Lcol = ny;
+  t.Ecol = fs::col_E(ny, f64);
+  t.Lz = nz;
+  t.Ez = fs::col_E(nz, f64);
+  size_t o = 0;
+  t.k2x = o;
+  o = align16(o + rs * (nx / 2 + 1));
+  t.k2y = o;
+  o = align16(o + rs * ny);
+  t.k2z = o;
+  o = align16(o + rs * nz);
+  t.tw_row = o;
+  o = align16(o + cs * fs::pass_table_size(t.Lrow, t.Erow));
+  t.tw_col = o;
+  o = align16(o + cs * fs::pass_table_size(t.Lcol, t.Ecol));
+  t.tw_z = o;
+  o = align16(o + cs * (nz > 1 ? fs::pass_table_size(t.Lz, t.Ez) : 0));
+  t.tw_half = o;
+  o = align16(o + cs * (nx / 2));
+  t.total = o;
+  return t;
+}
+
+size_t member_table_bytes(const fs_params& prm, bool f64) { return table_layout(prm, f64).total; }
+
+// Stockham pass tables of a line FFT of length L with E values per thread:
+// for every pass after the first (sub-length NS, radix R = min(E, L/NS)),
+// entries [j][r] = exp(-2 pi i r j / (NS R)), j < NS, r < R.
+void pass_table(int L, int E, std::vector<long double>& re, std::vector<long double>& im) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int ns = 1; ns < L;) {
+    int r = E < L / ns ? E : L / ns;
+    if (ns > 1)
+      for (int j = 0; j < ns; ++j)
+        for (int q = 0; q < r; ++q) {
+          long long e = (long long)q * j % ((long long)ns * r);
+          long double ang = 2.0L * pi * (long double)e / (long double)(ns * r);
+          re.push_back(cosl(ang));
+          im.push_back(-sinl(ang));
+        }
+    ns *= r;
+  }
+}
+
+template <typename T>
+void put_real(std::vector<char>& buf, size_t off, const std::vector<double>& v) {
+  T* d = reinterpret_cast<T*>(buf.data() + off);
+  for (size_t i = 0; i < v.size(); ++i) d[i] = (T)v[i];
+}
+template <typename T>
+void put_cplx(std::vector<char>& buf, size_t off, const std::vector<long double>& re,
+              const std::vector<long double>& im) {
+  T* d = reinterpret_cast<T*>(buf.data() + off);
+  for (size_t i = 0; i < re.size(); ++i) {
+    d[2 * i] = (T)re[i];
+    d[2 * i + 1] = (T)im[i];
+  }
+}
+
+cudaError_t upload_tables(Member& m, bool f64, char* dev, size_t bytes) {
+  const fs_params& prm = m.prm;
+  TableLayout t = table_layout(prm, f64);
+  std::vector<char> buf(bytes, 0);
+  int nx = prm.n[0], ny = prm.n[1], nz = prm.ndim > 2 ? prm.n[2] : 1;
+  std::vector<double> kx(nx / 2 + 1), ky(ny), kz(nz, 0.0);
+  for (int k = 0; k <= nx / 2; ++k) kx[k] = axis_k2(prm.lap, k, nx, prm.dx[0]);
+  for (int k = 0; k < ny; ++k) ky[k] = axis_k2(prm.lap, k, ny, prm.dx[1]);
+  for (int k = 0; k < nz && prm.ndim > 2; ++k) kz[k] = axis_k2(prm.lap, k, nz, prm.dx[2]);
+  std::vector<long double> rr, ii, cr, ci, zr, zi, hr, hi;
+  pass_table(t.Lrow, t.Erow, rr, ii);
+  pass_table(t.Lcol, t.Ecol, cr, ci);
+  if (nz > 1) pass_table(t.Lz, t.Ez, zr, zi);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int k = 0; k < nx / 2; ++k) {
+    long double ang = 2.0L * pi * (long double)k / (long double)nx;
+    hr.push_back(cosl(ang));
+    hi.push_back(-sinl(ang));
+  }
+  if (f64) {
+    put_real<double>(buf, t.k2x, kx);
+    put_real<double>(buf, t.k2y, ky);
+    put_real<double>(buf, t.k2z, kz);
+    put_cplx<double>(buf, t.tw_row, rr, ii);
+    put_cplx<double>(buf, t.tw_col, cr, ci);
+    put_cplx<double>(buf, t.tw_z, zr, zi);
+    put_cplx<double>(buf, t.tw_half, hr, hi);
+  } else {
+    put_real<float>(buf, t.k2x, kx);
+    put_real<float>(buf, t.k2y, ky);
+    put_real<float>(buf, t.k2z, kz);
+    put_cplx<float>(buf, t.tw_row, rr, ii);
+    put_cplx<float>(buf, t.tw_col, cr, ci);
+    put_cplx<float>(buf, t.tw_z, zr, zi);
+    put_cplx<float>(buf, t.tw_half, hr, hi);
+  }
+  m.k2x = dev + t.k2x;
+  m.k2y = dev + t.k2y;
+  m.k2z = dev + t.k2z;
+  m.tw_row = dev + t.tw_row;
+  m.tw_col = dev + t.tw_col;
+  m.tw_z = dev + t.tw_z;
+  m.tw_half = dev + t.tw_half;
+  return cudaMemcpy(dev, buf.data(), bytes, cudaMemcpyHostToDevice);
+}
+
 fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc_fn alloc, fs_free_fn dealloc,
                         void* ctx, fs_plan_t* out) {
   if (!out) return fail(nullptr, FS_ERR_INVALID_ARG, "out is NULL");
@@ -314,6 +443,7 @@ fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc
 
   // Workspace first (through the allocator hook), then tables.
   p->members.resize(count);
+  std::vector<size_t> table_bytes(count);
   for (int i = 0; i < count; ++i) {
     Member& m = p->members[i];
     m.prm = each[i];
@@ -322,20 +452,18 @@ fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc
     m.slot_stride = m.npts / 2;
     m.spec = plan_alloc(p, (size_t)(p->nf + 1) * m.slot_stride * cs);
     m.real = plan_alloc(p, (size_t)p->nf * m.npts * rs);
-    int nx = m.prm.n[0], ny = m.prm.n[1], nz = m.prm.ndim > 2 ? m.prm.n[2] : 1;
-    m.k2x = (double*)plan_alloc(p, sizeof(double) * (nx + ny + nz + 2));
+    table_bytes[i] = member_table_bytes(m.prm, p->f64);
+    char* tb = (char*)plan_alloc(p, table_bytes[i]);
     m.csum = (double*)plan_alloc(p, sizeof(double) * 8);
-    if (!m.spec || !m.real || !m.k2x || !m.csum) {
+    if (!m.spec || !m.real || !tb || !m.csum) {
       plan_free_all(p);
       delete p;
       return fail(nullptr, FS_ERR_OOM, "device workspace allocation failed");
     }
-    m.k2y = m.k2x + nx;
-    m.k2z = m.k2y + ny;
+    m.k2x = tb;  // the rest of the table pointers are set by upload_tables
   }
-  p->tw = plan_alloc(p, (size_t)fs::kTwN * cs);
   p->flag = (int*)plan_alloc(p, 256);
-  if (!p->tw || !p->flag) {
+  if (!p->flag) {
     plan_free_all(p);
     delete p;
     return fail(nullptr, FS_ERR_OOM, "device workspace allocation failed");
@@ -346,32 +474,9 @@ fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc
     delete p;
     return cuda_fail(nullptr, e, "cudaMallocHost");
   }
-
-  // Twiddles exp(-2 pi i j / kTwN), long double on the host.
-  {
-    const long double pi = 3.141592653589793238462643383279502884L;
-    std::vector<double> twd(2 * fs::kTwN);
-    for (int j = 0; j < fs::kTwN; ++j) {
-      long double ang = 2.0L * pi * (long double)j / (long double)fs::kTwN;
-      twd[2 * j] = (double)cosl(ang);
-      twd[2 * j + 1] = (double)(-sinl(ang));
-    }
-    if (p->f64) {
-      e = cudaMemcpy(p->tw, twd.data(), twd.size() * sizeof(double), cudaMemcpyHostToDevice);
-    } else {
-      std::vector<float> twf(twd.begin(), twd.end());
-      e = cudaMemcpy(p->tw, twf.data(), twf.size() * sizeof(float), cudaMemcpyHostToDevice);
-    }
-  }
-  for (Member& m : p->members) {
-    if (e != cudaSuccess) break;
-    int nx = m.prm.n[0], ny = m.prm.n[1], nz = m.prm.ndim > 2 ? m.prm.n[2] : 1;
-    std::vector<double> k2(nx + ny + nz + 2, 0.0);
-    for (int k = 0; k <= nx / 2; ++k) k2[k] = axis_k2(m.prm.lap, k, nx, m.prm.dx[0]);
-    for (int k = 0; k < ny; ++k) k2[nx + k] = axis_k2(m.prm.lap, k, ny, m.prm.dx[1]);
-    for (int k = 0; k < nz && m.prm.ndim > 2; ++k) k2[nx + ny + k] = axis_k2(m.prm.lap, k, nz, m.prm.dx[2]);
-    e = cudaMemcpy(m.k2x, k2.data(), k2.size() * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(m.csum, 0, sizeof(double) * 8);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    e = upload_tables(p->members[i], p->f64, (char*)p->members[i].k2x, table_bytes[i]);
+    if (e == cudaSuccess) e = cudaMemset(p->members[i].csum, 0, sizeof(double) * 8);
   }
   if (e == cudaSuccess) e = cudaMemset(p->flag, 0, 256);
   if (e != cudaSuccess) {
