@@ -5,14 +5,13 @@
 
 namespace fs {
 
-// Complex values per thread of a row (x) line FFT of length L = nx / 2.
-constexpr int row_E(int L, bool f64) { return L < (f64 ? 8 : 16) ? L : (f64 ? 8 : 16); }
+// Complex values per thread of a row (x) line FFT of length L = nx / 2:
+// 16, or fewer for short rows; at most 32 threads per line.
+constexpr int row_E(int L, bool f64) { return L < 16 ? L : (L / 16 > 32 ? L / 32 : 16); }
+// Rows per row-pass CTA: one warp covers 32 / TPL rows of one field.
+constexpr int row_R(int L, bool f64) { return 32 / (L / row_E(L, f64)); }
 // Complex values per thread of a column (y or z) line FFT of length L.
 constexpr int col_E(int L, bool f64) { return L < (f64 ? 8 : 16) ? L : (f64 ? 8 : 16); }
-// Threads per row-pass CTA (at least one row).
-constexpr int row_threads(int L, bool f64) {
-  return (L / row_E(L, f64)) > 128 ? (L / row_E(L, f64)) : 128;
-}
 // Columns per column-pass CTA: about 256 threads, at most 32 columns.
 constexpr int col_tk(int L, bool f64) {
   return (256 / (L / col_E(L, f64))) < 1 ? 1 : ((256 / (L / col_E(L, f64))) > 32 ? 32 : (256 / (L / col_E(L, f64))));

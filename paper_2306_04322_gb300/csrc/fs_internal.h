@@ -2,6 +2,7 @@
 // translation units.  Not part of the public C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -42,8 +43,10 @@ struct KArgs {
 // Return cudaErrorInvalidValue for a size without an instantiation.
 cudaError_t row_launch_f32(const KArgs& a, cudaStream_t s);
 cudaError_t row_launch_f64(const KArgs& a, cudaStream_t s);
-cudaError_t col_launch_f32(const KArgs& a, cudaStream_t s);
-cudaError_t col_launch_f64(const KArgs& a, cudaStream_t s);
+cudaError_t col_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
+cudaError_t col_launch_f64(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
+// Columns per CTA of the 2D column pass for this grid (the TMA box width).
+int col_tile_width(bool f64, int nx, int ny);
 // FP64 sum of n values of x (float or double) added into *out.
 cudaError_t sum_launch_f32(const void* x, long long n, double* out, cudaStream_t s);
 cudaError_t sum_launch_f64(const void* x, long long n, double* out, cudaStream_t s);

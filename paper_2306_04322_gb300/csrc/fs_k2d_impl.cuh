@@ -21,27 +21,32 @@ cudaError_t allow_big_smem(K kernel, unsigned* done_mask) {
 template <typename T, int NX>
 cudaError_t row_launch_n(const KArgs& a, cudaStream_t s) {
   using Cfg = RowCfg<T, NX>;
-  long long rpc = Cfg::THREADS / Cfg::TPL;
-  if (rpc > a.lines) rpc = a.lines;
-  size_t smem = Cfg::BAR_BYTES + (size_t)rpc * a.nf * Cfg::PL * sizeof(cplx<T>);
+  const long long reff = a.lines < Cfg::R ? a.lines : Cfg::R;
+  size_t smem = Cfg::BAR_BYTES + (size_t)(a.nf + 1) * Cfg::R * Cfg::PL * sizeof(cplx<T>);
   static unsigned done = 0;
   cudaError_t e = allow_big_smem(fs_row_kernel<T, NX>, &done);
   if (e != cudaSuccess) return e;
-  fs_row_kernel<T, NX><<<(unsigned)(a.lines / rpc), (unsigned)(rpc * Cfg::TPL), smem, s>>>(a);
+  fs_row_kernel<T, NX><<<(unsigned)(a.lines / reff), (unsigned)(32 * (a.nf + 1)), smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T, int NY>
-cudaError_t col_launch_n(const KArgs& a, cudaStream_t s) {
+int col_tk_n(int nx) {
   using Cfg = ColCfg<T, NY>;
-  int Lh = a.nx / 2;
-  int tk = Cfg::TK < Lh ? Cfg::TK : Lh;
-  size_t smem = 2 * (size_t)NY * tk * sizeof(cplx<T>);
+  int Lh = nx / 2;
+  return Cfg::TK < Lh ? Cfg::TK : Lh;
+}
+
+template <typename T, int NY>
+cudaError_t col_launch_n(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+  using Cfg = ColCfg<T, NY>;
+  const int tk = col_tk_n<T, NY>(a.nx);
+  size_t smem = Cfg::BAR_BYTES + 2 * (size_t)NY * tk * sizeof(cplx<T>);
   static unsigned done = 0;
   cudaError_t e = allow_big_smem(fs_col_kernel<T, NY>, &done);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)(Lh / tk), (unsigned)a.nf);
-  fs_col_kernel<T, NY><<<grid, (unsigned)(tk * Cfg::TPL), smem, s>>>(a);
+  dim3 grid((unsigned)(a.nx / 2 / tk), (unsigned)a.nf);
+  fs_col_kernel<T, NY><<<grid, (unsigned)(tk * Cfg::TPL), smem, s>>>(a, tm);
   return cudaGetLastError();
 }
 
@@ -61,17 +66,32 @@ cudaError_t row_launch_t(const KArgs& a, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t col_launch_t(const KArgs& a, cudaStream_t s) {
+cudaError_t col_launch_t(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
   switch (a.ny) {
-    case 8: return col_launch_n<T, 8>(a, s);
-    case 16: return col_launch_n<T, 16>(a, s);
-    case 32: return col_launch_n<T, 32>(a, s);
-    case 64: return col_launch_n<T, 64>(a, s);
-    case 128: return col_launch_n<T, 128>(a, s);
-    case 256: return col_launch_n<T, 256>(a, s);
-    case 512: return col_launch_n<T, 512>(a, s);
-    case 1024: return col_launch_n<T, 1024>(a, s);
+    case 8: return col_launch_n<T, 8>(a, tm, s);
+    case 16: return col_launch_n<T, 16>(a, tm, s);
+    case 32: return col_launch_n<T, 32>(a, tm, s);
+    case 64: return col_launch_n<T, 64>(a, tm, s);
+    case 128: return col_launch_n<T, 128>(a, tm, s);
+    case 256: return col_launch_n<T, 256>(a, tm, s);
+    case 512: return col_launch_n<T, 512>(a, tm, s);
+    case 1024: return col_launch_n<T, 1024>(a, tm, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+int col_tk_t(int nx, int ny) {
+  switch (ny) {
+    case 8: return col_tk_n<T, 8>(nx);
+    case 16: return col_tk_n<T, 16>(nx);
+    case 32: return col_tk_n<T, 32>(nx);
+    case 64: return col_tk_n<T, 64>(nx);
+    case 128: return col_tk_n<T, 128>(nx);
+    case 256: return col_tk_n<T, 256>(nx);
+    case 512: return col_tk_n<T, 512>(nx);
+    case 1024: return col_tk_n<T, 1024>(nx);
+    default: return 0;
   }
 }
 

@@ -67,8 +67,14 @@ __device__ __forceinline__ bool finite_val(T x) {
 }
 
 // ---------------------------------------------------------------------------
-// Row pass.  Lines along x; TPL threads per row, rpc rows per CTA.
-// Shared memory: rpc mbarriers, then per row nf slots of PL complex values.
+// Row pass.  Lines along x.  A CTA holds R rows and nf + 1 warps; warp w
+// works on field w of all R rows (TPL = L / E threads per line, 32 / TPL lines
+// per warp), so the independent transforms of the fields run in parallel:
+//   load    one thread issues bulk-async copies of every field's R rows
+//           (packed half spectra, or real pairs in mode 1) into the slots;
+//   phase 1 warp f < nf: inverse x transform of field f (modes 0 and 2);
+//   phase 2 all threads: pointwise stage, df/dc into slot nf, g_i over eta_i;
+//   phase 3 warp o <= nf: forward x transform of slot o to global memory.
 // Slot contents use the natural layout (element i at i) except during the
 // FFT exchanges, which use the padded layout (element i at pad32(i)).
 // mode 0: step, previous state in spec slots 0..nf-1 (y-inverted spectra)
@@ -84,149 +90,149 @@ struct RowCfg {
   static constexpr int L = NX / 2;
   static constexpr int E = row_E(L, F64);
   static constexpr int TPL = L / E;
+  static constexpr int R = row_R(L, F64);                 // rows per CTA
   static constexpr int PL = (padded_len(L) + 1) & ~1;  // even: 16-byte aligned slots
-  static constexpr int THREADS = row_threads(L, F64);
-  static constexpr int BAR_BYTES = 1024;  // room for the mbarriers of up to 128 rows
+  static constexpr int MAX_THREADS = 6 * 32;            // nf + 1 <= 6 warps
+  static constexpr int MIN_BLOCKS = F64 ? 2 : 4;
+  static constexpr int BAR_BYTES = 128;
 };
 
 template <typename T, int NX>
-__global__ void __launch_bounds__(RowCfg<T, NX>::THREADS) fs_row_kernel(KArgs a) {
+__global__ void __launch_bounds__(RowCfg<T, NX>::MAX_THREADS, RowCfg<T, NX>::MIN_BLOCKS)
+    fs_row_kernel(KArgs a) {
   using C = cplx<T>;
   using Cfg = RowCfg<T, NX>;
-  constexpr int L = Cfg::L, E = Cfg::E, TPL = Cfg::TPL, PL = Cfg::PL;
+  constexpr int L = Cfg::L, E = Cfg::E, TPL = Cfg::TPL, R = Cfg::R, PL = Cfg::PL;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  C* slots = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);  // [(nf + 1) * R][PL]
   const int nf = a.nf;
-  const int rl = threadIdx.x / TPL, t = threadIdx.x % TPL;
-  const int rpc = blockDim.x / TPL;
-  const long long row = (long long)blockIdx.x * rpc + rl;
-  C* slots = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES) + (size_t)rl * nf * PL;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / TPL, t = lane % TPL;  // row within the CTA, thread within the line
+  const int Reff = a.lines < R ? (int)a.lines : R;  // rows this CTA really holds
+  const bool active = g < Reff;
+  const long long row0 = (long long)blockIdx.x * Reff;
+  const long long row = row0 + g;
   const C* __restrict__ twr = reinterpret_cast<const C*>(a.tw_row);
   const C* __restrict__ twh = reinterpret_cast<const C*>(a.tw_half);
   C* spec = reinterpret_cast<C*>(a.spec);
   C* realc = reinterpret_cast<C*>(a.real);  // real row as complex pairs
   const long long half_stride = a.npts / 2;  // complex pairs per real field
-  auto sync = []() {
-    if constexpr (TPL == 32) __syncwarp(); else __syncthreads();
-  };
+  auto wsync = []() { __syncwarp(); };
+  auto slot = [slots](int f, int r) { return slots + (f * R + r) * PL; };
 
-  // 1. bulk-async load of every field's row (spectra or real pairs)
-  uint64_t* bar = bars + rl;
-  if (t == 0) {
+  // load: the R rows of field f are contiguous in global memory
+  if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
   }
   __syncthreads();
-  if (t == 0) {
+  if (threadIdx.x == 0) {
     const uint32_t bytes = (uint32_t)(L * sizeof(C));
-    mbar_arrive_expect_tx(bar, bytes * nf);
+    mbar_arrive_expect_tx(bar, bytes * Reff * nf);
     for (int f = 0; f < nf; ++f) {
-      const C* src = (a.mode == 1) ? realc + f * half_stride + row * L : spec + f * a.slot_stride + row * L;
-      bulk_g2s(slots + f * PL, src, bytes, bar);
+      const C* src = (a.mode == 1) ? realc + f * half_stride + row0 * L : spec + f * a.slot_stride + row0 * L;
+      for (int r = 0; r < Reff; ++r) bulk_g2s(slot(f, r), src + r * L, bytes, bar);
     }
   }
   if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
-    if (t == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
+    if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
     mbar_wait_bounded(bar, 0, kWaitPolls);  // let the copies land before exiting
     return;
   }
 
-  // 2. inverse x transforms (real pairs x[2j], x[2j+1] back into the slots)
-  if (a.mode != 1) {
-    for (int f = 0; f < nf; ++f) {
-      C* s = slots + f * PL;
-      auto st = [s](int i, C v) { s[pad32(i)] = v; };
-      auto ld = [s](int i) { return s[pad32(i)]; };
-      C v[E];
+  // phase 1: inverse x transforms (real pairs x[2j], x[2j+1] back into the slots)
+  if (a.mode != 1 && w < nf) {
+    C* s = slot(w, g);
+    auto st = [s](int i, C v) { s[pad32(i)] = v; };
+    auto ld = [s](int i) { return s[pad32(i)]; };
+    C v[E];
 #pragma unroll
-      for (int m = 0; m < E; ++m) {
-        const int k = t + TPL * m;
-        const C pk = s[k];
-        if (k == 0) {
-          v[m] = mk<C>(pk.x + pk.y, pk.x - pk.y);
-        } else {
-          const C pm = cconj(s[L - k]);
-          const C A = cadd(pk, pm), B = csub(pk, pm);
-          v[m] = cadd(A, mul_i<1>(mul_tw<1>(B, __ldg(&twh[k]))));
-        }
-      }
-      line_fft<L, E, 1>(v, t, twr, st, ld, sync);
-      if (a.mode == 2) {
-        C* dst = realc + f * half_stride + row * L;
-#pragma unroll
-        for (int m = 0; m < E; ++m) dst[t + TPL * m] = v[m];
+    for (int m = 0; m < E; ++m) {
+      const int k = t + TPL * m;
+      const C pk = s[k];
+      if (k == 0) {
+        v[m] = mk<C>(pk.x + pk.y, pk.x - pk.y);
       } else {
-        sync();
-#pragma unroll
-        for (int m = 0; m < E; ++m) s[t + TPL * m] = v[m];
+        const C pm = cconj(s[L - k]);
+        const C A = cadd(pk, pm), B = csub(pk, pm);
+        v[m] = cadd(A, mul_i<1>(mul_tw<1>(B, __ldg(&twh[k]))));
       }
     }
-    if (a.mode == 2) return;
+    line_fft<L, E, 1>(v, t, twr, st, ld, wsync);
+    if (a.mode == 2) {
+      C* dst = realc + w * half_stride + row * L;
+      if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) dst[t + TPL * m] = v[m];
+      }
+    } else {
+      wsync();
+#pragma unroll
+      for (int m = 0; m < E; ++m) s[t + TPL * m] = v[m];
+    }
   }
+  if (a.mode == 2) return;
+  __syncthreads();
 
-  // 3. pointwise derivative stage on the thread's own points:
-  //    df/dc kept in registers, g_i written over eta_i
-  C fcv[E];
+  // phase 2: pointwise derivative stage, all threads over all R * L pairs
   bool bad = false;
   {
     const Pointwise<T> pw(a);
     const int p = nf - 1;
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int i0 = t + TPL * m;
-      const C c = slots[i0];
+    for (int idx = threadIdx.x; idx < Reff * L; idx += blockDim.x) {
+      const int r = idx / L, i0 = idx % L;
+      const C c = slot(0, r)[i0];
       C h = mk<C>(T(0), T(0)), S2 = mk<C>(T(0), T(0));
       bad |= !(finite_val(c.x) && finite_val(c.y));
       for (int i = 0; i < p; ++i) {
-        const C e = slots[(1 + i) * PL + i0];
+        const C e = slot(1 + i, r)[i0];
         h.x += pw.hpoly(e.x);
         h.y += pw.hpoly(e.y);
         S2.x += e.x * e.x;
         S2.y += e.y * e.y;
         bad |= !(finite_val(e.x) && finite_val(e.y));
       }
-      fcv[m] = mk<C>(pw.fc(c.x, h.x), pw.fc(c.y, h.y));
+      slot(nf, r)[i0] = mk<C>(pw.fc(c.x, h.x), pw.fc(c.y, h.y));
       for (int i = 0; i < p; ++i) {
-        const C e = slots[(1 + i) * PL + i0];
-        slots[(1 + i) * PL + i0] =
+        const C e = slot(1 + i, r)[i0];
+        slot(1 + i, r)[i0] =
             mk<C>(e.x - pw.Ldt * pw.feta(c.x, e.x, S2.x), e.y - pw.Ldt * pw.feta(c.y, e.y, S2.y));
       }
     }
   }
+  __syncthreads();
 
-  // 4. forward x transforms of c, g_1..g_p (slots) and df/dc (registers),
-  //    packed half spectra scaled by 2, straight to global memory
-  for (int o = 0; o <= nf; ++o) {
-    C* s = slots + (o < nf ? o : 0) * PL;
+  // phase 3: forward x transform of slot w (c, g_1..g_p, df/dc), packed half
+  // spectra scaled by 2, straight to global memory
+  {
+    C* s = slot(w, g);
     auto st = [s](int i, C v) { s[pad32(i)] = v; };
     auto ld = [s](int i) { return s[pad32(i)]; };
     C v[E];
-    if (o < nf) {
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = s[t + TPL * m];
-    } else {
-#pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = fcv[m];
-    }
-    line_fft<L, E, -1>(v, t, twr, st, ld, sync);
-    sync();
+    for (int m = 0; m < E; ++m) v[m] = s[t + TPL * m];
+    line_fft<L, E, -1>(v, t, twr, st, ld, wsync);
+    wsync();
 #pragma unroll
     for (int m = 0; m < E; ++m) s[t + TPL * m] = v[m];
-    sync();
-    C* P = spec + o * a.slot_stride + row * L;
+    wsync();
+    C* P = spec + w * a.slot_stride + row * L;
+    if (active) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int k = t + TPL * m;
-      const C zk = s[k];
-      C out;
-      if (k == 0) {
-        out = mk<C>(T(2) * (zk.x + zk.y), T(2) * (zk.x - zk.y));
-      } else {
-        const C zm = cconj(s[L - k]);
-        const C A = cadd(zk, zm), B = csub(zk, zm);
-        out = cadd(A, mul_i<-1>(cmul(B, __ldg(&twh[k]))));
+      for (int m = 0; m < E; ++m) {
+        const int k = t + TPL * m;
+        const C zk = s[k];
+        C out;
+        if (k == 0) {
+          out = mk<C>(T(2) * (zk.x + zk.y), T(2) * (zk.x - zk.y));
+        } else {
+          const C zm = cconj(s[L - k]);
+          const C A = cadd(zk, zm), B = csub(zk, zm);
+          out = cadd(A, mul_i<-1>(cmul(B, __ldg(&twh[k]))));
+        }
+        P[k] = out;
       }
-      P[k] = out;
     }
   }
   if (bad) atomicOr(a.flag, FS_FLAG_NONFINITE);
@@ -235,10 +241,11 @@ __global__ void __launch_bounds__(RowCfg<T, NX>::THREADS) fs_row_kernel(KArgs a)
 // ---------------------------------------------------------------------------
 // Column pass (2D step).  Lines along y of the packed x-spectra; one CTA per
 // tile of tk adjacent kx columns (TPL threads per column) and per field group
-// (blockIdx.y = 0: c with df/dc, g >= 1: eta_g).  Forward y transforms,
-// k-space update, inverse y transforms, in place.
-// Shared memory: exchange tile [NY][tk] and, for the c group, the forward
-// transform of df/dc [NY][tk].
+// (blockIdx.y = 0: c with df/dc, g >= 1: eta_g).  The tiles [NY][tk] of the
+// group's slots arrive by TMA (3D tensor map over [slot][y][kx]); then
+// forward y transforms, k-space update and inverse y transforms, stored in
+// place.  Each loaded tile is also the exchange buffer of its own transform;
+// for the c group the transformed df/dc stays in tile 0 for the update.
 // ---------------------------------------------------------------------------
 template <typename T, int NY>
 struct ColCfg {
@@ -247,6 +254,8 @@ struct ColCfg {
   static constexpr int TPL = NY / E;
   static constexpr int TK = col_tk(NY, F64);
   static constexpr int THREADS = TPL * TK;
+  static constexpr int BH = NY < 256 ? NY : 256;  // TMA box height (rows)
+  static constexpr int BAR_BYTES = 128;
 };
 
 template <typename T>
@@ -270,44 +279,66 @@ struct KUpdate {
 };
 
 template <typename T, int NY>
-__global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2) fs_col_kernel(KArgs a) {
+__global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
+    fs_col_kernel(KArgs a, const __grid_constant__ CUtensorMap tmap) {
   using C = cplx<T>;
   using Cfg = ColCfg<T, NY>;
-  constexpr int E = Cfg::E, TPL = Cfg::TPL;
+  constexpr int E = Cfg::E, TPL = Cfg::TPL, BH = Cfg::BH;
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  C* tiles = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);
   const int tk = blockDim.x / TPL;  // columns in this CTA (<= TK)
-  C* tile = reinterpret_cast<C*>(smem_raw);
-  C* stash = tile + NY * tk;
   const int j = threadIdx.x % tk, t = threadIdx.x / tk;
   const int Lh = a.nx / 2;
   const int kx0 = blockIdx.x * tk;
   const int kx = kx0 + j;
   const int g = blockIdx.y;  // field group
   const int nf = a.nf;
+  const int nin = (g == 0) ? 2 : 1;
   const C* __restrict__ twc = reinterpret_cast<const C*>(a.tw_col);
   const T* __restrict__ k2xt = reinterpret_cast<const T*>(a.k2x);
   const T* __restrict__ k2yt = reinterpret_cast<const T*>(a.k2y);
-  C* base = reinterpret_cast<C*>(a.spec) + kx;
-  auto st = [tile, tk, j](int i, C v) { tile[i * tk + j] = v; };
-  auto ld = [tile, tk, j](int i) { return tile[i * tk + j]; };
-  auto sync = []() { __syncthreads(); };
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(bar, (uint32_t)(nin * NY * tk * sizeof(C)));
+    const int cx = kx0 * (int)(sizeof(C) / 8);  // innermost coordinate in 8-byte units
+    for (int i = 0; i < nin; ++i) {
+      const int slot = (g == 0) ? (i == 0 ? nf : 0) : g;
+      for (int y0 = 0; y0 < NY; y0 += BH) tma_load_3d(tiles + (i * NY + y0) * tk, &tmap, cx, y0, slot, bar);
+    }
+  }
+  if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
+    if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
+    mbar_wait_bounded(bar, 0, kWaitPolls);
+    return;
+  }
+
   const KUpdate<T> up(a);
   const bool special = (kx0 == 0);  // CTA holding the packed DC/Nyquist column
   const T kx2 = k2xt[kx];
   const T kxn2 = k2xt[Lh];  // Nyquist column
+  C* stash = tiles;  // c group: transformed df/dc, natural layout [ky][j]
+  C* xt = tiles + (nin - 1) * NY * tk;  // exchange tile of the updated field
+  auto sync = []() { __syncthreads(); };
 
-  // forward transforms: c group takes df/dc (slot nf, kept in `stash`) then c
-  const int nin = (g == 0) ? 2 : 1;
+  // forward transforms: c group takes df/dc (tile 0) then c (tile 1)
   C v[E];
   for (int i = 0; i < nin; ++i) {
-    const int slot = (g == 0) ? (i == 0 ? nf : 0) : g;
-    const C* S = base + (long long)slot * a.slot_stride;
+    C* tl = tiles + i * NY * tk + j;
+    auto st = [tl, tk](int q, C x) { tl[q * tk] = x; };
+    auto ld = [tl, tk](int q) { return tl[q * tk]; };
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = S[(long long)(t + TPL * m) * Lh];
+    for (int m = 0; m < E; ++m) v[m] = tl[(t + TPL * m) * tk];
     line_fft<NY, E, -1>(v, t, twc, st, ld, sync);
-    if (g == 0 && i == 0) {
+    if (i == 0 && nin == 2) {
+      sync();
 #pragma unroll
-      for (int m = 0; m < E; ++m) stash[(t + TPL * m) * tk + j] = v[m];
+      for (int m = 0; m < E; ++m) tl[(t + TPL * m) * tk] = v[m];
     }
   }
 
@@ -317,7 +348,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2) fs_col_kernel(KArgs
     sync();
     if (j == 0) {
 #pragma unroll
-      for (int m = 0; m < E; ++m) tile[(t + TPL * m) * tk] = v[m];
+      for (int m = 0; m < E; ++m) xt[(t + TPL * m) * tk] = v[m];
     }
     sync();
   }
@@ -326,7 +357,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2) fs_col_kernel(KArgs
     for (int m = 0; m < E; ++m) {
       const int ky = t + TPL * m, kq = (NY - ky) & (NY - 1);
       const T ky2 = k2yt[ky];
-      const C pz = cconj(tile[kq * tk]);
+      const C pz = cconj(xt[kq * tk]);
       const C A = cscale(cadd(v[m], pz), T(0.5)), B = cscale(mul_i<-1>(csub(v[m], pz)), T(0.5));
       C An, Bn;
       if (g == 0) {
@@ -352,8 +383,13 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2) fs_col_kernel(KArgs
     for (int m = 0; m < E; ++m) v[m] = up.eta(v[m], kx2 + k2yt[t + TPL * m]);
   }
 
-  line_fft<NY, E, 1>(v, t, twc, st, ld, sync);
-  C* S = base + (long long)(g == 0 ? 0 : g) * a.slot_stride;
+  {
+    C* tl = xt + j;
+    auto st = [tl, tk](int q, C x) { tl[q * tk] = x; };
+    auto ld = [tl, tk](int q) { return tl[q * tk]; };
+    line_fft<NY, E, 1>(v, t, twc, st, ld, sync);
+  }
+  C* S = reinterpret_cast<C*>(a.spec) + kx + (long long)(g == 0 ? 0 : g) * a.slot_stride;
 #pragma unroll
   for (int m = 0; m < E; ++m) S[(long long)(t + TPL * m) * Lh] = v[m];
 }

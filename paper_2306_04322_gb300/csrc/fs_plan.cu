@@ -35,6 +35,7 @@ struct Member {
   void* tw_half = nullptr;
   double* csum = nullptr;
   long long slot_stride = 0;
+  CUtensorMap tmap_col;  // [slot][y][kx] tiles of the 2D column pass
 };
 
 }  // namespace
@@ -229,8 +230,46 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
 cudaError_t launch_row(const fs_plan* p, const fs::KArgs& a, cudaStream_t s) {
   return p->f64 ? fs::row_launch_f64(a, s) : fs::row_launch_f32(a, s);
 }
-cudaError_t launch_col(const fs_plan* p, const fs::KArgs& a, cudaStream_t s) {
-  return p->f64 ? fs::col_launch_f64(a, s) : fs::col_launch_f32(a, s);
+cudaError_t launch_col(const fs_plan* p, const Member& m, const fs::KArgs& a, cudaStream_t s) {
+  return p->f64 ? fs::col_launch_f64(a, m.tmap_col, s) : fs::col_launch_f32(a, m.tmap_col, s);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  return fn;
+}
+
+// Tensor map over the spectrum slots viewed as [nf + 1][ny][W] 8-byte units
+// (W = nx/2 for FP32 complex, nx for FP64 complex); box = one column tile of
+// the column pass, up to 256 rows.
+bool encode_col_map(Member& m, int nslots, bool f64) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const int units = f64 ? 2 : 1;
+  const int nx = m.prm.n[0], ny = m.prm.n[1] * (m.prm.ndim > 2 ? m.prm.n[2] : 1);
+  const int tk = fs::col_tile_width(f64, nx, m.prm.n[1]);
+  cuuint64_t dims[3] = {(cuuint64_t)(nx / 2) * units, (cuuint64_t)ny, (cuuint64_t)nslots};
+  cuuint64_t strides[2] = {(cuuint64_t)(nx / 2) * units * 8, (cuuint64_t)(nx / 2) * units * 8 * ny};
+  cuuint32_t box[3] = {(cuuint32_t)(tk * units), (cuuint32_t)(m.prm.n[1] < 256 ? m.prm.n[1] : 256), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(&m.tmap_col, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, m.spec, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 // One time step of every member: row pass then column pass.
@@ -239,7 +278,7 @@ cudaError_t enqueue_step(fs_plan* p, int mode, cudaStream_t s, int64_t* launches
     fs::KArgs a = make_args(p, m, mode);
     cudaError_t e = launch_row(p, a, s);
     if (e != cudaSuccess) return e;
-    e = launch_col(p, a, s);
+    e = launch_col(p, m, a, s);
     if (e != cudaSuccess) return e;
     *launches += 2;
   }
@@ -477,6 +516,7 @@ fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc
   for (int i = 0; i < count && e == cudaSuccess; ++i) {
     e = upload_tables(p->members[i], p->f64, (char*)p->members[i].k2x, table_bytes[i]);
     if (e == cudaSuccess) e = cudaMemset(p->members[i].csum, 0, sizeof(double) * 8);
+    if (e == cudaSuccess && !encode_col_map(p->members[i], p->nf + 1, p->f64)) e = cudaErrorInvalidValue;
   }
   if (e == cudaSuccess) e = cudaMemset(p->flag, 0, 256);
   if (e != cudaSuccess) {
@@ -667,7 +707,7 @@ fs_status fs_step_profiled(fs_plan_t p, int64_t nsteps) {
       if (e == cudaSuccess) e = launch_row(p, a, p->stream);
       rec(0);
       rec(1);
-      if (e == cudaSuccess) e = launch_col(p, a, p->stream);
+      if (e == cudaSuccess) e = launch_col(p, m, a, p->stream);
       rec(1);
       launches += 2;
     }
