@@ -12,9 +12,9 @@
 // P passes costs P - 1 shared-memory round trips and no global traffic.
 //
 // Twiddles: per-pass tables built on the host in long double, laid out
-// [pass][j][r] with r = 0..R-1 (entry r = 0 is 1), so a thread reads the
-// R - 1 twiddles of its butterfly as consecutive values.  No device
-// trigonometry is used.
+// [pass][r][j] (r = 0..R-1, j = 0..NS-1; entries r = 0 are 1), so the lanes
+// of a warp, which hold consecutive j, read consecutive entries.  Kernels
+// copy the tables to shared memory first.  No device trigonometry is used.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -195,9 +195,9 @@ __device__ __forceinline__ void stockham(C (&v)[E], int t, const C* __restrict__
     const int b = t + TPL * q;
     if constexpr (NS > 1) {
       const int j = b & (NS - 1);
-      const C* w = twp + pass_table_offset<L, E, NS>() + j * R;
+      const C* w = twp + pass_table_offset<L, E, NS>() + j;
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[q + Q * r] = mul_tw<DIR>(v[q + Q * r], __ldg(&w[r]));
+      for (int r = 1; r < R; ++r) v[q + Q * r] = mul_tw<DIR>(v[q + Q * r], w[r * NS]);
     }
     reg_dft<R, DIR, Q>(&v[q]);
   }
@@ -219,7 +219,8 @@ __device__ __forceinline__ void stockham(C (&v)[E], int t, const C* __restrict__
 }
 
 // Full line FFT, X[k] = sum_n x[n] exp(DIR 2 pi i n k / L), unnormalised.
-// twp: the pass tables of (L, E) (forward roots; the inverse conjugates).
+// twp: the pass tables of (L, E) (forward roots; the inverse conjugates),
+// usually a shared-memory copy.
 template <int L, int E, int DIR, typename C, class Store, class Load, class Sync>
 __device__ __forceinline__ void line_fft(C (&v)[E], int t, const C* __restrict__ twp, Store st, Load ld,
                                          Sync sync) {
@@ -231,6 +232,12 @@ __device__ __forceinline__ void line_fft(C (&v)[E], int t, const C* __restrict__
 // stride-R butterfly writes and the stride-TPL reads free of bank conflicts.
 __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 constexpr int padded_len(int L) { return L + L / 32 + 1; }
+
+// Cooperative copy of n complex values global -> shared (all threads).
+template <typename C>
+__device__ __forceinline__ void copy_to_smem(C* dst, const C* __restrict__ src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = __ldg(&src[i]);
+}
 
 // ---- asynchronous bulk copies and mbarriers (inline PTX, sm_90+) ----------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -15,6 +15,15 @@ enum : int { FS_FLAG_NONFINITE = 1, FS_FLAG_TIMEOUT = 2, FS_FLAG_BOUNDS = 4 };
 // Polls of an mbarrier before a wait gives up and reports FS_FLAG_TIMEOUT.
 constexpr uint32_t kWaitPolls = 1u << 20;
 
+// Scalar coefficients of the pointwise stage and the k-space update,
+// precomputed on the host in FP64 and stored in both precisions so the FP32
+// kernels issue no FP64 arithmetic.
+template <typename T>
+struct Coef {
+  T two_rho2, ca, dcab, rho2dcab, cab, w, four_alpha, Ldt;  // pointwise stage
+  T Mdt, Mdtkc, Ldtke, scale;                               // k-space update
+};
+
 // Arguments of one pass over one simulation (passed by value).  Array
 // pointers are in the plan's precision T (float or double) unless noted.
 struct KArgs {
@@ -37,7 +46,13 @@ struct KArgs {
   double inv_npts;         // 1 / N
   const double* csum;      // FP64 sum of c carried for the k = 0 mode (NULL: off)
   int* flag;               // sticky error bits (FS_FLAG_*)
+  Coef<float> cf;          // coefficients, FP32 copy
+  Coef<double> cd;         // coefficients, FP64 copy
 };
+
+template <typename T> __host__ __device__ inline const Coef<T>& coef(const KArgs& a);
+template <> __host__ __device__ inline const Coef<float>& coef<float>(const KArgs& a) { return a.cf; }
+template <> __host__ __device__ inline const Coef<double>& coef<double>(const KArgs& a) { return a.cd; }
 
 // Kernel launchers, one per precision (fs_k2d_f32.cu / fs_k2d_f64.cu).
 // Return cudaErrorInvalidValue for a size without an instantiation.

@@ -22,7 +22,7 @@ template <typename T, int NX>
 cudaError_t row_launch_n(const KArgs& a, cudaStream_t s) {
   using Cfg = RowCfg<T, NX>;
   const long long reff = a.lines < Cfg::R ? a.lines : Cfg::R;
-  size_t smem = Cfg::BAR_BYTES + (size_t)(a.nf + 1) * Cfg::R * Cfg::PL * sizeof(cplx<T>);
+  size_t smem = Cfg::BAR_BYTES + Cfg::TW_BYTES + (size_t)(a.nf + 1) * Cfg::R * Cfg::PL * sizeof(cplx<T>);
   static unsigned done = 0;
   cudaError_t e = allow_big_smem(fs_row_kernel<T, NX>, &done);
   if (e != cudaSuccess) return e;
@@ -41,7 +41,7 @@ template <typename T, int NY>
 cudaError_t col_launch_n(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
   using Cfg = ColCfg<T, NY>;
   const int tk = col_tk_n<T, NY>(a.nx);
-  size_t smem = Cfg::BAR_BYTES + 2 * (size_t)NY * tk * sizeof(cplx<T>);
+  size_t smem = Cfg::HEAD + 2 * (size_t)Cfg::TROWS * tk * sizeof(cplx<T>);
   static unsigned done = 0;
   cudaError_t e = allow_big_smem(fs_col_kernel<T, NY>, &done);
   if (e != cudaSuccess) return e;

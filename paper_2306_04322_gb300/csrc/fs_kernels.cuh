@@ -44,10 +44,17 @@ namespace fs {
 template <typename T>
 struct Pointwise {
   T two_rho2, ca, dcab, rho2dcab, cab, w, four_alpha, Ldt;
-  __device__ explicit Pointwise(const KArgs& a)
-      : two_rho2((T)(2.0 * a.rho2)), ca((T)a.c_alpha), dcab((T)(a.c_beta - a.c_alpha)),
-        rho2dcab((T)(a.rho2 * (a.c_beta - a.c_alpha))), cab((T)(a.c_beta + a.c_alpha)), w((T)a.w),
-        four_alpha((T)(4.0 * a.alpha)), Ldt((T)(a.L * a.dt)) {}
+  __device__ explicit Pointwise(const KArgs& a) {
+    const Coef<T>& k = coef<T>(a);
+    two_rho2 = k.two_rho2;
+    ca = k.ca;
+    dcab = k.dcab;
+    rho2dcab = k.rho2dcab;
+    cab = k.cab;
+    w = k.w;
+    four_alpha = k.four_alpha;
+    Ldt = k.Ldt;
+  }
   __device__ __forceinline__ T hpoly(T e) const { return e * e * e * (e * (T(6) * e - T(15)) + T(10)); }
   __device__ __forceinline__ T dh(T e) const {
     T q = e * (T(1) - e);
@@ -95,6 +102,8 @@ struct RowCfg {
   static constexpr int MAX_THREADS = 6 * 32;            // nf + 1 <= 6 warps
   static constexpr int MIN_BLOCKS = F64 ? 2 : 4;
   static constexpr int BAR_BYTES = 128;
+  static constexpr int TWS = pass_table_size(L, E);  // twiddle entries (complex)
+  static constexpr int TW_BYTES = ((TWS * (int)sizeof(cplx<T>)) + 127) & ~127;
 };
 
 template <typename T, int NX>
@@ -105,7 +114,8 @@ __global__ void __launch_bounds__(RowCfg<T, NX>::MAX_THREADS, RowCfg<T, NX>::MIN
   constexpr int L = Cfg::L, E = Cfg::E, TPL = Cfg::TPL, R = Cfg::R, PL = Cfg::PL;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  C* slots = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);  // [(nf + 1) * R][PL]
+  C* twr = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);
+  C* slots = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES + Cfg::TW_BYTES);  // [(nf + 1) * R][PL]
   const int nf = a.nf;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / TPL, t = lane % TPL;  // row within the CTA, thread within the line
@@ -113,12 +123,12 @@ __global__ void __launch_bounds__(RowCfg<T, NX>::MAX_THREADS, RowCfg<T, NX>::MIN
   const bool active = g < Reff;
   const long long row0 = (long long)blockIdx.x * Reff;
   const long long row = row0 + g;
-  const C* __restrict__ twr = reinterpret_cast<const C*>(a.tw_row);
   const C* __restrict__ twh = reinterpret_cast<const C*>(a.tw_half);
   C* spec = reinterpret_cast<C*>(a.spec);
   C* realc = reinterpret_cast<C*>(a.real);  // real row as complex pairs
   const long long half_stride = a.npts / 2;  // complex pairs per real field
   auto wsync = []() { __syncwarp(); };
+  copy_to_smem(twr, reinterpret_cast<const C*>(a.tw_row), Cfg::TWS);
   auto slot = [slots](int f, int r) { return slots + (f * R + r) * PL; };
 
   // load: the R rows of field f are contiguous in global memory
@@ -256,14 +266,25 @@ struct ColCfg {
   static constexpr int THREADS = TPL * TK;
   static constexpr int BH = NY < 256 ? NY : 256;  // TMA box height (rows)
   static constexpr int BAR_BYTES = 128;
+  static constexpr int TWS = pass_table_size(NY, E);  // twiddle entries (complex)
+  static constexpr int TW_BYTES = ((TWS * (int)sizeof(cplx<T>)) + 127) & ~127;
+  static constexpr int K2_BYTES = ((NY * (int)sizeof(T)) + 127) & ~127;
+  static constexpr int LOGE = ilog2(E);
+  // tile rows: NY natural rows plus room for the padded exchange layout
+  static constexpr int TROWS = (NY + NY / E + 1 + 15) & ~15;
+  static constexpr int HEAD = BAR_BYTES + TW_BYTES + K2_BYTES;
 };
 
 template <typename T>
 struct KUpdate {
   T Mdt, Mdtkc, Ldtke, scale;
-  __device__ explicit KUpdate(const KArgs& a)
-      : Mdt((T)(a.M * a.dt)), Mdtkc((T)(a.M * a.dt * a.kappa_c)), Ldtke((T)(a.L * a.dt * a.kappa_eta)),
-        scale((T)a.scale) {}
+  __device__ explicit KUpdate(const KArgs& a) {
+    const Coef<T>& k = coef<T>(a);
+    Mdt = k.Mdt;
+    Mdtkc = k.Mdtkc;
+    Ldtke = k.Ldtke;
+    scale = k.scale;
+  }
   // c^' = (c^ - M dt K2 f^) / (1 + M dt kappa_c K2^2), times the 1/(2N) scale
   template <typename C>
   __device__ __forceinline__ C c(C zc, C zf, T k2) const {
@@ -284,9 +305,12 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
   using C = cplx<T>;
   using Cfg = ColCfg<T, NY>;
   constexpr int E = Cfg::E, TPL = Cfg::TPL, BH = Cfg::BH;
+  constexpr int TROWS = Cfg::TROWS, LOGE = Cfg::LOGE;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  C* tiles = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);
+  C* twc = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);
+  T* k2yt = reinterpret_cast<T*>(smem_raw + Cfg::BAR_BYTES + Cfg::TW_BYTES);
+  C* tiles = reinterpret_cast<C*>(smem_raw + Cfg::HEAD);
   const int tk = blockDim.x / TPL;  // columns in this CTA (<= TK)
   const int j = threadIdx.x % tk, t = threadIdx.x / tk;
   const int Lh = a.nx / 2;
@@ -295,9 +319,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
   const int g = blockIdx.y;  // field group
   const int nf = a.nf;
   const int nin = (g == 0) ? 2 : 1;
-  const C* __restrict__ twc = reinterpret_cast<const C*>(a.tw_col);
   const T* __restrict__ k2xt = reinterpret_cast<const T*>(a.k2x);
-  const T* __restrict__ k2yt = reinterpret_cast<const T*>(a.k2y);
 
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -309,9 +331,12 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
     const int cx = kx0 * (int)(sizeof(C) / 8);  // innermost coordinate in 8-byte units
     for (int i = 0; i < nin; ++i) {
       const int slot = (g == 0) ? (i == 0 ? nf : 0) : g;
-      for (int y0 = 0; y0 < NY; y0 += BH) tma_load_3d(tiles + (i * NY + y0) * tk, &tmap, cx, y0, slot, bar);
+      for (int y0 = 0; y0 < NY; y0 += BH) tma_load_3d(tiles + (i * TROWS + y0) * tk, &tmap, cx, y0, slot, bar);
     }
   }
+  copy_to_smem(twc, reinterpret_cast<const C*>(a.tw_col), Cfg::TWS);
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) k2yt[i] = reinterpret_cast<const T*>(a.k2y)[i];
+  __syncthreads();
   if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
     mbar_wait_bounded(bar, 0, kWaitPolls);
@@ -323,15 +348,15 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
   const T kx2 = k2xt[kx];
   const T kxn2 = k2xt[Lh];  // Nyquist column
   C* stash = tiles;  // c group: transformed df/dc, natural layout [ky][j]
-  C* xt = tiles + (nin - 1) * NY * tk;  // exchange tile of the updated field
+  C* xt = tiles + (nin - 1) * TROWS * tk;  // exchange tile of the updated field
   auto sync = []() { __syncthreads(); };
 
   // forward transforms: c group takes df/dc (tile 0) then c (tile 1)
   C v[E];
   for (int i = 0; i < nin; ++i) {
-    C* tl = tiles + i * NY * tk + j;
-    auto st = [tl, tk](int q, C x) { tl[q * tk] = x; };
-    auto ld = [tl, tk](int q) { return tl[q * tk]; };
+    C* tl = tiles + i * TROWS * tk + j;
+    auto st = [tl, tk](int q, C x) { tl[(q + (q >> LOGE)) * tk] = x; };
+    auto ld = [tl, tk](int q) { return tl[(q + (q >> LOGE)) * tk]; };
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = tl[(t + TPL * m) * tk];
     line_fft<NY, E, -1>(v, t, twc, st, ld, sync);
@@ -385,8 +410,8 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
 
   {
     C* tl = xt + j;
-    auto st = [tl, tk](int q, C x) { tl[q * tk] = x; };
-    auto ld = [tl, tk](int q) { return tl[q * tk]; };
+    auto st = [tl, tk](int q, C x) { tl[(q + (q >> LOGE)) * tk] = x; };
+    auto ld = [tl, tk](int q) { return tl[(q + (q >> LOGE)) * tk]; };
     line_fft<NY, E, 1>(v, t, twc, st, ld, sync);
   }
   C* S = reinterpret_cast<C*>(a.spec) + kx + (long long)(g == 0 ? 0 : g) * a.slot_stride;

@@ -190,6 +190,22 @@ void plan_free_all(fs_plan* p) {
   p->ws_bytes = 0;
 }
 
+template <typename T>
+void fill_coef(fs::Coef<T>& k, const fs_params& q, double scale) {
+  k.two_rho2 = (T)(2.0 * q.rho2);
+  k.ca = (T)q.c_alpha;
+  k.dcab = (T)(q.c_beta - q.c_alpha);
+  k.rho2dcab = (T)(q.rho2 * (q.c_beta - q.c_alpha));
+  k.cab = (T)(q.c_beta + q.c_alpha);
+  k.w = (T)q.w;
+  k.four_alpha = (T)(4.0 * q.alpha);
+  k.Ldt = (T)(q.L * q.dt);
+  k.Mdt = (T)(q.M * q.dt);
+  k.Mdtkc = (T)(q.M * q.dt * q.kappa_c);
+  k.Ldtke = (T)(q.L * q.dt * q.kappa_eta);
+  k.scale = (T)scale;
+}
+
 fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   fs::KArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -224,6 +240,8 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   a.inv_npts = 1.0 / (double)m.npts;
   a.csum = p->f64 ? nullptr : m.csum;
   a.flag = p->flag;
+  fill_coef(a.cd, m.prm, a.scale);
+  fill_coef(a.cf, m.prm, a.scale);
   return a;
 }
 
@@ -377,14 +395,14 @@ size_t member_table_bytes(const fs_params& prm, bool f64) { return table_layout(
 
 // Stockham pass tables of a line FFT of length L with E values per thread:
 // for every pass after the first (sub-length NS, radix R = min(E, L/NS)),
-// entries [j][r] = exp(-2 pi i r j / (NS R)), j < NS, r < R.
+// entries [r][j] = exp(-2 pi i r j / (NS R)), r < R, j < NS.
 void pass_table(int L, int E, std::vector<long double>& re, std::vector<long double>& im) {
   const long double pi = 3.141592653589793238462643383279502884L;
   for (int ns = 1; ns < L;) {
     int r = E < L / ns ? E : L / ns;
     if (ns > 1)
-      for (int j = 0; j < ns; ++j)
-        for (int q = 0; q < r; ++q) {
+      for (int q = 0; q < r; ++q)
+        for (int j = 0; j < ns; ++j) {
           long long e = (long long)q * j % ((long long)ns * r);
           long double ang = 2.0L * pi * (long double)e / (long double)(ns * r);
           re.push_back(cosl(ang));
