@@ -22,6 +22,7 @@ template <typename T>
 struct Coef {
   T two_rho2, ca, dcab, rho2dcab, cab, w, four_alpha, Ldt;  // pointwise stage
   T Mdt, Mdtkc, Ldtke, scale;                               // k-space update
+  T idx2, idy2, idz2, kc, ke, dtM, dtL;                     // explicit FD scheme
 };
 
 // Arguments of one pass over one simulation (passed by value).  Array
@@ -62,6 +63,8 @@ cudaError_t col_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s
 cudaError_t col_launch_f64(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
 // Columns per CTA of the 2D column pass for this grid (the TMA box width).
 int col_tile_width(bool f64, int nx, int ny);
+// One explicit finite-difference step (fs_fd.cu): in -> out, nf fields each.
+cudaError_t fd_launch(bool f64, const KArgs& a, const void* in, void* out, cudaStream_t s);
 // FP64 sum of n values of x (float or double) added into *out.
 cudaError_t sum_launch_f32(const void* x, long long n, double* out, cudaStream_t s);
 cudaError_t sum_launch_f64(const void* x, long long n, double* out, cudaStream_t s);

@@ -36,6 +36,7 @@ struct Member {
   double* csum = nullptr;
   long long slot_stride = 0;
   CUtensorMap tmap_col;  // [slot][y][kx] tiles of the 2D column pass
+  int fd_cur = 0;        // explicit FD: 0 state in `real`, 1 state in `spec` (as real fields)
 };
 
 }  // namespace
@@ -43,6 +44,7 @@ struct Member {
 struct fs_plan {
   std::vector<Member> members;
   bool f64 = true;
+  bool fd = false;  // explicit FD comparison scheme
   int nf = 1;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -140,8 +142,8 @@ fs_status validate(const fs_params* p, std::string* why) {
     *why = "3D grids are not built in this library version";
     return FS_ERR_UNSUPPORTED;
   }
-  if (p->scheme != FS_SCHEME_SEMI_IMPLICIT_FS) {
-    *why = "explicit FD scheme is not built in this library version";
+  if (p->scheme == FS_SCHEME_EXPLICIT_FD && p->ndim != 2) {
+    *why = "the explicit FD comparison scheme is built for 2D grids";
     return FS_ERR_UNSUPPORTED;
   }
   if (p->precision == FS_F32_TC_TF32 || p->precision == FS_F32_TC_BF16X3) {
@@ -192,6 +194,13 @@ void plan_free_all(fs_plan* p) {
 
 template <typename T>
 void fill_coef(fs::Coef<T>& k, const fs_params& q, double scale) {
+  k.idx2 = (T)(1.0 / (q.dx[0] * q.dx[0]));
+  k.idy2 = (T)(1.0 / (q.dx[1] * q.dx[1]));
+  k.idz2 = (T)(q.ndim > 2 ? 1.0 / (q.dx[2] * q.dx[2]) : 0.0);
+  k.kc = (T)q.kappa_c;
+  k.ke = (T)q.kappa_eta;
+  k.dtM = (T)(q.dt * q.M);
+  k.dtL = (T)(q.dt * q.L);
   k.two_rho2 = (T)(2.0 * q.rho2);
   k.ca = (T)q.c_alpha;
   k.dcab = (T)(q.c_beta - q.c_alpha);
@@ -290,8 +299,21 @@ bool encode_col_map(Member& m, int nslots, bool f64) {
   return r == CUDA_SUCCESS;
 }
 
-// One time step of every member: row pass then column pass.
+void* fd_buf(const Member& m, int which) { return which == 0 ? m.real : m.spec; }
+
+// One time step of every member: row pass then column pass (or one explicit
+// FD step, ping-ponging between the two real-field buffers).
 cudaError_t enqueue_step(fs_plan* p, int mode, cudaStream_t s, int64_t* launches) {
+  if (p->fd) {
+    for (Member& m : p->members) {
+      fs::KArgs a = make_args(p, m, 0);
+      cudaError_t e = fs::fd_launch(p->f64, a, fd_buf(m, m.fd_cur), fd_buf(m, 1 - m.fd_cur), s);
+      if (e != cudaSuccess) return e;
+      m.fd_cur = 1 - m.fd_cur;
+      *launches += 1;
+    }
+    return cudaSuccess;
+  }
   for (const Member& m : p->members) {
     fs::KArgs a = make_args(p, m, mode);
     cudaError_t e = launch_row(p, a, s);
@@ -482,14 +504,16 @@ fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc
     std::string why;
     fs_status s = validate(&each[i], &why);
     if (s != FS_OK) return fail(nullptr, s, count > 1 ? "member " + std::to_string(i) + ": " + why : why);
-    if (each[i].precision != each[0].precision || each[i].p != each[0].p)
-      return fail(nullptr, FS_ERR_INVALID_ARG, "batch members must share precision and p");
+    if (each[i].precision != each[0].precision || each[i].p != each[0].p ||
+        each[i].scheme != each[0].scheme)
+      return fail(nullptr, FS_ERR_INVALID_ARG, "batch members must share precision, p and scheme");
   }
   if ((alloc == nullptr) != (dealloc == nullptr))
     return fail(nullptr, FS_ERR_INVALID_ARG, "alloc and dealloc must both be given or both NULL");
 
   fs_plan* p = new fs_plan();
   p->f64 = each[0].precision == FS_F64;
+  p->fd = each[0].scheme == FS_SCHEME_EXPLICIT_FD;
   p->nf = 1 + each[0].p;
   p->stream = reinterpret_cast<cudaStream_t>(stream);
   p->alloc = alloc;
@@ -577,7 +601,8 @@ fs_status fs_set_fields(fs_plan_t p, const void* const* fields) {
       cudaError_t e = cudaMemcpyAsync(dst, fields[idx], m.npts * rs, cudaMemcpyDefault, p->stream);
       if (e != cudaSuccess) return cuda_fail(p, e, "fs_set_fields copy");
     }
-    if (!p->f64) {
+    m.fd_cur = 0;
+    if (!p->f64 && !p->fd) {
       cudaError_t e = cudaMemsetAsync(m.csum, 0, sizeof(double), p->stream);
       if (e == cudaSuccess) e = fs::sum_launch_f32(m.real, m.npts, m.csum, p->stream);
       if (e != cudaSuccess) return cuda_fail(p, e, "fs_set_fields mean carry");
@@ -594,14 +619,14 @@ fs_status fs_step_async(fs_plan_t p, int64_t nsteps) {
   int64_t launches = 0;
   int64_t done = 0;
   cudaError_t e = cudaSuccess;
-  if (nsteps > 0 && p->state == kStateReal) {
+  if (nsteps > 0 && p->state == kStateReal && !p->fd) {
     e = enqueue_step(p, 1, p->stream, &launches);
     if (e != cudaSuccess) return cuda_fail(p, e, "step launch");
     done = 1;
     p->state = kStateSpec;
   }
   int64_t left = nsteps - done;
-  if (left >= kGraphSteps) {
+  if (left >= kGraphSteps && !p->fd) {
     if (!p->gexec) {
       e = build_graph(p);
       if (e != cudaSuccess) return cuda_fail(p, e, "graph capture");
@@ -617,7 +642,7 @@ fs_status fs_step_async(fs_plan_t p, int64_t nsteps) {
     e = enqueue_step(p, 0, p->stream, &launches);
     if (e != cudaSuccess) return cuda_fail(p, e, "step launch");
   }
-  if (nsteps > 0) p->state = kStateSpec;
+  if (nsteps > 0 && !p->fd) p->state = kStateSpec;
   p->last_launches = launches;
   return FS_OK;
 }
@@ -637,7 +662,7 @@ fs_status fs_get_fields(fs_plan_t p, void* const* out) {
   if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
   if (!out) return fail(p, FS_ERR_INVALID_ARG, "fields_out is NULL");
   if (p->state == kStateNone) return fail(p, FS_ERR_STATE, "fs_get_fields before fs_set_fields");
-  if (p->state == kStateSpec) {
+  if (p->state == kStateSpec && !p->fd) {
     for (const Member& m : p->members) {
       fs::KArgs a = make_args(p, m, 2);
       cudaError_t e = launch_row(p, a, p->stream);
@@ -650,7 +675,7 @@ fs_status fs_get_fields(fs_plan_t p, void* const* out) {
   for (const Member& m : p->members)
     for (int f = 0; f < p->nf; ++f, ++idx) {
       if (!out[idx]) return fail(p, FS_ERR_INVALID_ARG, "output pointer is NULL");
-      const char* src = (const char*)m.real + (size_t)f * m.npts * rs;
+      const char* src = (const char*)(p->fd ? fd_buf(m, m.fd_cur) : m.real) + (size_t)f * m.npts * rs;
       cudaError_t e = cudaMemcpyAsync(out[idx], src, m.npts * rs, cudaMemcpyDefault, p->stream);
       if (e != cudaSuccess) return cuda_fail(p, e, "fs_get_fields copy");
     }
@@ -717,6 +742,20 @@ fs_status fs_step_profiled(fs_plan_t p, int64_t nsteps) {
     if (e == cudaSuccess) p->ev_used++;
   };
   int64_t launches = 0;
+  if (p->fd) {
+    for (int64_t s = 0; s < nsteps && e == cudaSuccess; ++s)
+      for (Member& m : p->members) {
+        fs::KArgs a = make_args(p, m, 0);
+        rec(0);
+        if (e == cudaSuccess) e = fs::fd_launch(p->f64, a, fd_buf(m, m.fd_cur), fd_buf(m, 1 - m.fd_cur), p->stream);
+        rec(0);
+        m.fd_cur = 1 - m.fd_cur;
+        launches++;
+      }
+    if (e != cudaSuccess) return cuda_fail(p, e, "fs_step_profiled");
+    p->last_launches = launches;
+    return FS_OK;
+  }
   for (int64_t s = 0; s < nsteps && e == cudaSuccess; ++s) {
     int mode = p->state == kStateReal ? 1 : 0;
     for (const Member& m : p->members) {
