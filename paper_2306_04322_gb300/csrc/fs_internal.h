@@ -63,6 +63,15 @@ cudaError_t col_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s
 cudaError_t col_launch_f64(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
 // Columns per CTA of the 2D column pass for this grid (the TMA box width).
 int col_tile_width(bool f64, int nx, int ny);
+// 3D passes (fs_k3d_f32.cu / fs_k3d_f64.cu): y transform of nslots slots of
+// every z plane (dir -1 forward with kx = 0 column packing, +1 inverse), and
+// the z step (forward z, k-space update, inverse z).
+cudaError_t ypass_launch_f32(const KArgs& a, const CUtensorMap& tm, int dir, int nslots, cudaStream_t s);
+cudaError_t ypass_launch_f64(const KArgs& a, const CUtensorMap& tm, int dir, int nslots, cudaStream_t s);
+cudaError_t zstep_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
+cudaError_t zstep_launch_f64(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
+int line_tile_width_f32(int nx, int nl);
+int line_tile_width_f64(int nx, int nl);
 // One explicit finite-difference step (fs_fd.cu): in -> out, nf fields each.
 cudaError_t fd_launch(bool f64, const KArgs& a, const void* in, void* out, cudaStream_t s);
 // FP64 sum of n values of x (float or double) added into *out.

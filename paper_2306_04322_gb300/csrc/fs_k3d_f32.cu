@@ -1,0 +1,13 @@
+// float instantiations of the 3D y / z passes.
+#include "fs_k2d_impl.cuh"
+#include "fs_k3d_impl.cuh"
+
+namespace fs {
+cudaError_t ypass_launch_f32(const KArgs& a, const CUtensorMap& tm, int dir, int nslots, cudaStream_t s) {
+  return ypass_launch_t<float>(a, tm, dir, nslots, s);
+}
+cudaError_t zstep_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+  return zstep_launch_t<float>(a, tm, s);
+}
+int line_tile_width_f32(int nx, int nl) { return line_tk_t<float>(nx, nl); }
+}  // namespace fs

@@ -35,7 +35,8 @@ struct Member {
   void* tw_half = nullptr;
   double* csum = nullptr;
   long long slot_stride = 0;
-  CUtensorMap tmap_col;  // [slot][y][kx] tiles of the 2D column pass
+  CUtensorMap tmap_col;  // [slot * nz + z][y][kx] tiles of the 2D column pass / 3D y passes
+  CUtensorMap tmap_z;    // [slot][z][y][kx] z lines of the 3D z step
   int fd_cur = 0;        // explicit FD: 0 state in `real`, 1 state in `spec` (as real fields)
 };
 
@@ -138,8 +139,8 @@ fs_status validate(const fs_params* p, std::string* why) {
       *why = "each grid axis must be a power of two in [8, 1024]";
       return FS_ERR_UNSUPPORTED;
     }
-  if (p->ndim == 3) {
-    *why = "3D grids are not built in this library version";
+  if (p->ndim == 3 && (p->n[1] > 512 || p->n[2] > 512)) {
+    *why = "3D grids support y and z axes up to 512";
     return FS_ERR_UNSUPPORTED;
   }
   if (p->scheme == FS_SCHEME_EXPLICIT_FD && p->ndim != 2) {
@@ -287,17 +288,40 @@ bool encode_col_map(Member& m, int nslots, bool f64) {
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return false;
   const int units = f64 ? 2 : 1;
-  const int nx = m.prm.n[0], ny = m.prm.n[1] * (m.prm.ndim > 2 ? m.prm.n[2] : 1);
-  const int tk = fs::col_tile_width(f64, nx, m.prm.n[1]);
-  cuuint64_t dims[3] = {(cuuint64_t)(nx / 2) * units, (cuuint64_t)ny, (cuuint64_t)nslots};
-  cuuint64_t strides[2] = {(cuuint64_t)(nx / 2) * units * 8, (cuuint64_t)(nx / 2) * units * 8 * ny};
-  cuuint32_t box[3] = {(cuuint32_t)(tk * units), (cuuint32_t)(m.prm.n[1] < 256 ? m.prm.n[1] : 256), 1};
-  cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(&m.tmap_col, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, m.spec, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
+  const int nx = m.prm.n[0], ny = m.prm.n[1], nz = m.prm.ndim > 2 ? m.prm.n[2] : 1;
+  const cuuint64_t W = (cuuint64_t)(nx / 2) * units;  // 8-byte units per row
+  {
+    // [slot * nz + z][y][kx]: column tiles of the 2D column pass / 3D y passes
+    const int tk = nz > 1 ? (f64 ? fs::line_tile_width_f64(nx, ny) : fs::line_tile_width_f32(nx, ny))
+                          : fs::col_tile_width(f64, nx, ny);
+    cuuint64_t dims[3] = {W, (cuuint64_t)ny, (cuuint64_t)nz * nslots};
+    cuuint64_t strides[2] = {W * 8, W * 8 * ny};
+    cuuint32_t box[3] = {(cuuint32_t)(tk * units), (cuuint32_t)(ny < 256 ? ny : 256), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&m.tmap_col, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, m.spec, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+  }
+  if (nz > 1) {
+    // [slot][z][y][kx]: z lines of one (ky, kx tile), up to 256 planes per box
+    const int tk = f64 ? fs::line_tile_width_f64(nx, nz) : fs::line_tile_width_f32(nx, nz);
+    cuuint64_t dims[4] = {W, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nslots};
+    cuuint64_t strides[3] = {W * 8, W * 8 * ny, W * 8 * ny * nz};
+    cuuint32_t box[4] = {(cuuint32_t)(tk * units), 1, (cuuint32_t)(nz < 256 ? nz : 256), 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(&m.tmap_z, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, m.spec, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+  }
+  return true;
 }
+
+// The passes of one step: 2D row, column; 3D x, y forward, z, y inverse.
+int pass_kinds(const Member& m) { return m.prm.ndim > 2 ? 4 : 2; }
+
+cudaError_t launch_pass(const fs_plan* p, const Member& m, const fs::KArgs& a, int kind, cudaStream_t s);
 
 void* fd_buf(const Member& m, int which) { return which == 0 ? m.real : m.spec; }
 
@@ -316,13 +340,24 @@ cudaError_t enqueue_step(fs_plan* p, int mode, cudaStream_t s, int64_t* launches
   }
   for (const Member& m : p->members) {
     fs::KArgs a = make_args(p, m, mode);
-    cudaError_t e = launch_row(p, a, s);
-    if (e != cudaSuccess) return e;
-    e = launch_col(p, m, a, s);
-    if (e != cudaSuccess) return e;
-    *launches += 2;
+    for (int k = 0; k < pass_kinds(m); ++k) {
+      cudaError_t e = launch_pass(p, m, a, k, s);
+      if (e != cudaSuccess) return e;
+      *launches += 1;
+    }
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_pass(const fs_plan* p, const Member& m, const fs::KArgs& a, int kind, cudaStream_t s) {
+  if (kind == 0) return launch_row(p, a, s);
+  if (m.prm.ndim == 2) return launch_col(p, m, a, s);
+  const int nf = p->nf;
+  if (kind == 1)
+    return p->f64 ? fs::ypass_launch_f64(a, m.tmap_col, -1, nf + 1, s)
+                  : fs::ypass_launch_f32(a, m.tmap_col, -1, nf + 1, s);
+  if (kind == 2) return p->f64 ? fs::zstep_launch_f64(a, m.tmap_z, s) : fs::zstep_launch_f32(a, m.tmap_z, s);
+  return p->f64 ? fs::ypass_launch_f64(a, m.tmap_col, 1, nf, s) : fs::ypass_launch_f32(a, m.tmap_col, 1, nf, s);
 }
 
 void drop_graph(fs_plan* p) {
@@ -760,13 +795,12 @@ fs_status fs_step_profiled(fs_plan_t p, int64_t nsteps) {
     int mode = p->state == kStateReal ? 1 : 0;
     for (const Member& m : p->members) {
       fs::KArgs a = make_args(p, m, mode);
-      rec(0);
-      if (e == cudaSuccess) e = launch_row(p, a, p->stream);
-      rec(0);
-      rec(1);
-      if (e == cudaSuccess) e = launch_col(p, m, a, p->stream);
-      rec(1);
-      launches += 2;
+      for (int k = 0; k < pass_kinds(m); ++k) {
+        rec(k);
+        if (e == cudaSuccess) e = launch_pass(p, m, a, k, p->stream);
+        rec(k);
+        launches++;
+      }
     }
     p->state = kStateSpec;
   }
@@ -779,9 +813,9 @@ fs_status fs_profile_read(fs_plan_t p, double* ms_per_pass, int64_t* launches_pe
                           int* npass) {
   if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
   if (!ms_per_pass || !npass || npass_max < 1) return fail(p, FS_ERR_INVALID_ARG, "bad arguments");
-  const int kinds = 2;
-  double ms[kinds] = {0.0, 0.0};
-  int64_t cnt[kinds] = {0, 0};
+  const int kinds = 4;
+  double ms[kinds] = {0.0, 0.0, 0.0, 0.0};
+  int64_t cnt[kinds] = {0, 0, 0, 0};
   cudaError_t e = cudaStreamSynchronize(p->stream);
   for (size_t i = 0; e == cudaSuccess && i + 1 < p->ev_used; i += 2) {
     float t = 0.f;
@@ -791,7 +825,8 @@ fs_status fs_profile_read(fs_plan_t p, double* ms_per_pass, int64_t* launches_pe
   }
   p->ev_used = 0;
   if (e != cudaSuccess) return cuda_fail(p, e, "fs_profile_read");
-  int n = kinds < npass_max ? kinds : npass_max;
+  int used = p->fd ? 1 : pass_kinds(p->members[0]);
+  int n = used < npass_max ? used : npass_max;
   for (int i = 0; i < n; ++i) {
     ms_per_pass[i] = ms[i];
     if (launches_per_pass) launches_per_pass[i] = cnt[i];
