@@ -163,6 +163,12 @@ fs_status fs_step_profiled(fs_plan_t plan, int64_t nsteps);
 fs_status fs_profile_read(fs_plan_t plan, double* ms_per_pass, int64_t* launches_per_pass, int npass_max,
                           int* npass);
 
+/* Batched plans: the persistent grid sizes (CTAs) of the row and column
+ * launches chosen by the autotuner (it runs inside the first fs_set_fields
+ * and times candidate grids on that state), and the work items of each. */
+fs_status fs_batch_schedule(fs_plan_t plan, int64_t* row_grid, int64_t* col_grid, int64_t* row_items,
+                            int64_t* col_items);
+
 /* Device bytes owned by the plan. */
 fs_status fs_workspace_bytes(fs_plan_t plan, size_t* bytes);
 

@@ -72,6 +72,32 @@ cudaError_t zstep_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t
 cudaError_t zstep_launch_f64(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
 int line_tile_width_f32(int nx, int nl);
 int line_tile_width_f64(int nx, int nl);
+// Batched ensemble launches (fs_batch_f32.cu / fs_batch_f64.cu).
+struct BatchArgs {
+  const KArgs* mem;             // per simulation, row-pass arguments (execution order)
+  const KArgs* mem_col;         // per simulation, column-pass arguments
+  const CUtensorMap* maps;      // per simulation, column tile tensor map
+  const long long* row_begin;   // first row work item of each simulation
+  const long long* col_begin;   // first column work item of each simulation
+  const int* col_tiles;         // kx tiles of each simulation
+  int nm;                       // simulations
+  int nf1;                      // nf + 1 (warps of a row CTA)
+  long long row_total, col_total;
+  long long row_grid, col_grid; // persistent grid sizes
+  size_t row_smem, col_smem;
+};
+cudaError_t row_batch_launch_f32(const BatchArgs& b, cudaStream_t s);
+cudaError_t row_batch_launch_f64(const BatchArgs& b, cudaStream_t s);
+cudaError_t col_batch_launch_f32(const BatchArgs& b, cudaStream_t s);
+cudaError_t col_batch_launch_f64(const BatchArgs& b, cudaStream_t s);
+size_t row_smem_f32(int nx, int nf);
+size_t row_smem_f64(int nx, int nf);
+long long row_blocks_f32(int nx, long long lines);
+long long row_blocks_f64(int nx, long long lines);
+int col_batch_tk_f32(int nx, int ny);
+int col_batch_tk_f64(int nx, int ny);
+size_t col_smem_f32(int ny, int tk);
+size_t col_smem_f64(int ny, int tk);
 // One explicit finite-difference step (fs_fd.cu): in -> out, nf fields each.
 cudaError_t fd_launch(bool f64, const KArgs& a, const void* in, void* out, cudaStream_t s);
 // FP64 sum of n values of x (float or double) added into *out.

@@ -106,14 +106,22 @@ struct RowCfg {
   static constexpr int TW_BYTES = ((TWS * (int)sizeof(cplx<T>)) + 127) & ~127;
 };
 
+// Shared memory of one row-pass CTA (bytes).
 template <typename T, int NX>
-__global__ void __launch_bounds__(RowCfg<T, NX>::MAX_THREADS, RowCfg<T, NX>::MIN_BLOCKS)
-    fs_row_kernel(KArgs a) {
+constexpr size_t row_smem_bytes(int nf) {
+  return RowCfg<T, NX>::BAR_BYTES + RowCfg<T, NX>::TW_BYTES +
+         (size_t)(nf + 1) * RowCfg<T, NX>::R * RowCfg<T, NX>::PL * sizeof(cplx<T>);
+}
+
+// One row-pass work item: row block rb of the simulation described by `a`.
+// `bar` is an initialised mbarrier whose next phase has parity `parity`.
+// Returns false if a bounded wait gave up (the caller must stop).
+template <typename T, int NX>
+__device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned char* smem_raw, uint64_t* bar,
+                                         uint32_t parity) {
   using C = cplx<T>;
   using Cfg = RowCfg<T, NX>;
   constexpr int L = Cfg::L, E = Cfg::E, TPL = Cfg::TPL, R = Cfg::R, PL = Cfg::PL;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   C* twr = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);
   C* slots = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES + Cfg::TW_BYTES);  // [(nf + 1) * R][PL]
   const int nf = a.nf;
@@ -121,7 +129,7 @@ __global__ void __launch_bounds__(RowCfg<T, NX>::MAX_THREADS, RowCfg<T, NX>::MIN
   const int g = lane / TPL, t = lane % TPL;  // row within the CTA, thread within the line
   const int Reff = a.lines < R ? (int)a.lines : R;  // rows this CTA really holds
   const bool active = g < Reff;
-  const long long row0 = (long long)blockIdx.x * Reff;
+  const long long row0 = rb * Reff;
   const long long row = row0 + g;
   const C* __restrict__ twh = reinterpret_cast<const C*>(a.tw_half);
   C* spec = reinterpret_cast<C*>(a.spec);
@@ -130,13 +138,9 @@ __global__ void __launch_bounds__(RowCfg<T, NX>::MAX_THREADS, RowCfg<T, NX>::MIN
   auto wsync = []() { __syncwarp(); };
   copy_to_smem(twr, reinterpret_cast<const C*>(a.tw_row), Cfg::TWS);
   auto slot = [slots](int f, int r) { return slots + (f * R + r) * PL; };
+  __syncthreads();
 
   // load: the R rows of field f are contiguous in global memory
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
   if (threadIdx.x == 0) {
     const uint32_t bytes = (uint32_t)(L * sizeof(C));
     mbar_arrive_expect_tx(bar, bytes * Reff * nf);
@@ -145,10 +149,10 @@ __global__ void __launch_bounds__(RowCfg<T, NX>::MAX_THREADS, RowCfg<T, NX>::MIN
       for (int r = 0; r < Reff; ++r) bulk_g2s(slot(f, r), src + r * L, bytes, bar);
     }
   }
-  if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
+  if (!mbar_wait_bounded(bar, parity, kWaitPolls)) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
-    mbar_wait_bounded(bar, 0, kWaitPolls);  // let the copies land before exiting
-    return;
+    mbar_wait_bounded(bar, parity, kWaitPolls);  // let the copies land before exiting
+    return false;
   }
 
   // phase 1: inverse x transforms (real pairs x[2j], x[2j+1] back into the slots)
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(RowCfg<T, NX>::MAX_THREADS, RowCfg<T, NX>::MIN
       for (int m = 0; m < E; ++m) s[t + TPL * m] = v[m];
     }
   }
-  if (a.mode == 2) return;
+  if (a.mode == 2) return true;
   __syncthreads();
 
   // phase 2: pointwise derivative stage, all threads over all R * L pairs
@@ -246,6 +250,20 @@ __global__ void __launch_bounds__(RowCfg<T, NX>::MAX_THREADS, RowCfg<T, NX>::MIN
     }
   }
   if (bad) atomicOr(a.flag, FS_FLAG_NONFINITE);
+  return true;
+}
+
+template <typename T, int NX>
+__global__ void __launch_bounds__(RowCfg<T, NX>::MAX_THREADS, RowCfg<T, NX>::MIN_BLOCKS)
+    fs_row_kernel(KArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  row_body<T, NX>(a, blockIdx.x, smem_raw, bar, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -299,48 +317,48 @@ struct KUpdate {
   }
 };
 
+// Shared memory of one column-pass CTA (bytes) for a tile of tk columns.
 template <typename T, int NY>
-__global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
-    fs_col_kernel(KArgs a, const __grid_constant__ CUtensorMap tmap) {
+constexpr size_t col_smem_bytes(int tk) {
+  return ColCfg<T, NY>::HEAD + 2 * (size_t)ColCfg<T, NY>::TROWS * tk * sizeof(cplx<T>);
+}
+
+// One column-pass work item: kx tile bx, field group g of the simulation
+// described by `a`, tiles loaded through the tensor map `tmap`.
+template <typename T, int NY>
+__device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap, int bx, int g,
+                                         unsigned char* smem_raw, uint64_t* bar, uint32_t parity) {
   using C = cplx<T>;
   using Cfg = ColCfg<T, NY>;
   constexpr int E = Cfg::E, TPL = Cfg::TPL, BH = Cfg::BH;
   constexpr int TROWS = Cfg::TROWS, LOGE = Cfg::LOGE;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   C* twc = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);
   T* k2yt = reinterpret_cast<T*>(smem_raw + Cfg::BAR_BYTES + Cfg::TW_BYTES);
   C* tiles = reinterpret_cast<C*>(smem_raw + Cfg::HEAD);
   const int tk = blockDim.x / TPL;  // columns in this CTA (<= TK)
   const int j = threadIdx.x % tk, t = threadIdx.x / tk;
   const int Lh = a.nx / 2;
-  const int kx0 = blockIdx.x * tk;
+  const int kx0 = bx * tk;
   const int kx = kx0 + j;
-  const int g = blockIdx.y;  // field group
   const int nf = a.nf;
   const int nin = (g == 0) ? 2 : 1;
   const T* __restrict__ k2xt = reinterpret_cast<const T*>(a.k2x);
 
   if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
     mbar_arrive_expect_tx(bar, (uint32_t)(nin * NY * tk * sizeof(C)));
     const int cx = kx0 * (int)(sizeof(C) / 8);  // innermost coordinate in 8-byte units
     for (int i = 0; i < nin; ++i) {
       const int slot = (g == 0) ? (i == 0 ? nf : 0) : g;
-      for (int y0 = 0; y0 < NY; y0 += BH) tma_load_3d(tiles + (i * TROWS + y0) * tk, &tmap, cx, y0, slot, bar);
+      for (int y0 = 0; y0 < NY; y0 += BH) tma_load_3d(tiles + (i * TROWS + y0) * tk, tmap, cx, y0, slot, bar);
     }
   }
   copy_to_smem(twc, reinterpret_cast<const C*>(a.tw_col), Cfg::TWS);
   for (int i = threadIdx.x; i < NY; i += blockDim.x) k2yt[i] = reinterpret_cast<const T*>(a.k2y)[i];
   __syncthreads();
-  if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
+  if (!mbar_wait_bounded(bar, parity, kWaitPolls)) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
-    mbar_wait_bounded(bar, 0, kWaitPolls);
-    return;
+    mbar_wait_bounded(bar, parity, kWaitPolls);
+    return false;
   }
 
   const KUpdate<T> up(a);
@@ -417,6 +435,20 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
   C* S = reinterpret_cast<C*>(a.spec) + kx + (long long)(g == 0 ? 0 : g) * a.slot_stride;
 #pragma unroll
   for (int m = 0; m < E; ++m) S[(long long)(t + TPL * m) * Lh] = v[m];
+  return true;
+}
+
+template <typename T, int NY>
+__global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
+    fs_col_kernel(KArgs a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  col_body<T, NY>(a, &tmap, blockIdx.x, blockIdx.y, smem_raw, bar, 0);
 }
 
 }  // namespace fs

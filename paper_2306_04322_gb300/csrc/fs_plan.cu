@@ -4,6 +4,7 @@
 // Boccardo et al., arXiv 2306.04322).  Kernels live in the fs_k*.cu units.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -46,6 +47,10 @@ struct fs_plan {
   std::vector<Member> members;
   bool f64 = true;
   bool fd = false;  // explicit FD comparison scheme
+  bool batch = false;  // ensemble: one launch per pass for all members
+  fs::BatchArgs bargs{};
+  const fs::KArgs* bmem1 = nullptr;  // row arguments in mode 1 (from real fields)
+  bool tuned = false;
   int nf = 1;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -325,6 +330,15 @@ cudaError_t launch_pass(const fs_plan* p, const Member& m, const fs::KArgs& a, i
 
 void* fd_buf(const Member& m, int which) { return which == 0 ? m.real : m.spec; }
 
+// Batched ensemble: kind 0 row pass (mode 0 from spectra, 1 from real
+// fields), kind 1 column pass, each one persistent launch for all members.
+cudaError_t launch_batch_pass(const fs_plan* p, int mode, int kind, cudaStream_t s) {
+  fs::BatchArgs b = p->bargs;
+  if (mode == 1) b.mem = p->bmem1;
+  if (kind == 0) return p->f64 ? fs::row_batch_launch_f64(b, s) : fs::row_batch_launch_f32(b, s);
+  return p->f64 ? fs::col_batch_launch_f64(b, s) : fs::col_batch_launch_f32(b, s);
+}
+
 // One time step of every member: row pass then column pass (or one explicit
 // FD step, ping-ponging between the two real-field buffers).
 cudaError_t enqueue_step(fs_plan* p, int mode, cudaStream_t s, int64_t* launches) {
@@ -334,6 +348,14 @@ cudaError_t enqueue_step(fs_plan* p, int mode, cudaStream_t s, int64_t* launches
       cudaError_t e = fs::fd_launch(p->f64, a, fd_buf(m, m.fd_cur), fd_buf(m, 1 - m.fd_cur), s);
       if (e != cudaSuccess) return e;
       m.fd_cur = 1 - m.fd_cur;
+      *launches += 1;
+    }
+    return cudaSuccess;
+  }
+  if (p->batch) {
+    for (int k = 0; k < 2; ++k) {
+      cudaError_t e = launch_batch_pass(p, mode, k, s);
+      if (e != cudaSuccess) return e;
       *launches += 1;
     }
     return cudaSuccess;
@@ -530,6 +552,126 @@ cudaError_t upload_tables(Member& m, bool f64, char* dev, size_t bytes) {
   return cudaMemcpy(dev, buf.data(), bytes, cudaMemcpyHostToDevice);
 }
 
+// ---- batched ensemble set-up ------------------------------------------------
+// Work lists in execution order (largest simulation first), argument blocks
+// for both row-pass modes, the column tensor maps, and the shared-memory size
+// of the largest member.  Requires 2D spectral-FS members whose column pass
+// fits the 256-thread batch CTA.
+fs_status setup_batch(fs_plan* p) {
+  const int nm = (int)p->members.size();
+  for (const Member& m : p->members) {
+    if (m.prm.ndim != 2 || m.prm.scheme != FS_SCHEME_SEMI_IMPLICIT_FS)
+      return fail(nullptr, FS_ERR_UNSUPPORTED, "batched plans hold 2D semi-implicit FS members");
+    const int nx = m.prm.n[0], ny = m.prm.n[1];
+    const int tk = p->f64 ? fs::col_batch_tk_f64(nx, ny) : fs::col_batch_tk_f32(nx, ny);
+    if (nx < 16 || tk == 0)
+      return fail(nullptr, FS_ERR_UNSUPPORTED, "batched members need nx >= 16 and ny >= 128 (FP32) / 64 (FP64)");
+  }
+  std::vector<int> order(nm);
+  for (int i = 0; i < nm; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [p](int a, int b) { return p->members[a].npts > p->members[b].npts; });
+  std::vector<fs::KArgs> k0(nm), k1(nm);
+  std::vector<CUtensorMap> maps(nm);
+  std::vector<long long> rb(nm + 1, 0), cb(nm + 1, 0);
+  std::vector<int> tiles(nm);
+  size_t rsm = 0, csm = 0;
+  for (int e = 0; e < nm; ++e) {
+    const Member& m = p->members[order[e]];
+    const int nx = m.prm.n[0], ny = m.prm.n[1];
+    k0[e] = make_args(p, m, 0);
+    k1[e] = make_args(p, m, 1);
+    maps[e] = m.tmap_col;
+    const long long blocks = p->f64 ? fs::row_blocks_f64(nx, ny) : fs::row_blocks_f32(nx, ny);
+    const int tk = p->f64 ? fs::col_batch_tk_f64(nx, ny) : fs::col_batch_tk_f32(nx, ny);
+    tiles[e] = nx / 2 / tk;
+    rb[e + 1] = rb[e] + blocks;
+    cb[e + 1] = cb[e] + (long long)tiles[e] * p->nf;
+    rsm = std::max(rsm, p->f64 ? fs::row_smem_f64(nx, p->nf) : fs::row_smem_f32(nx, p->nf));
+    csm = std::max(csm, p->f64 ? fs::col_smem_f64(ny, tk) : fs::col_smem_f32(ny, tk));
+  }
+  const size_t o_maps = 0, o_k0 = align16(o_maps + sizeof(CUtensorMap) * nm);
+  const size_t o_k1 = align16(o_k0 + sizeof(fs::KArgs) * nm), o_rb = align16(o_k1 + sizeof(fs::KArgs) * nm);
+  const size_t o_cb = align16(o_rb + sizeof(long long) * (nm + 1));
+  const size_t o_t = align16(o_cb + sizeof(long long) * (nm + 1)), total = align16(o_t + sizeof(int) * nm);
+  char* dev = (char*)plan_alloc(p, total);
+  if (!dev) return fail(nullptr, FS_ERR_OOM, "device workspace allocation failed");
+  std::vector<char> host(total, 0);
+  std::memcpy(host.data() + o_maps, maps.data(), sizeof(CUtensorMap) * nm);
+  std::memcpy(host.data() + o_k0, k0.data(), sizeof(fs::KArgs) * nm);
+  std::memcpy(host.data() + o_k1, k1.data(), sizeof(fs::KArgs) * nm);
+  std::memcpy(host.data() + o_rb, rb.data(), sizeof(long long) * (nm + 1));
+  std::memcpy(host.data() + o_cb, cb.data(), sizeof(long long) * (nm + 1));
+  std::memcpy(host.data() + o_t, tiles.data(), sizeof(int) * nm);
+  cudaError_t e = cudaMemcpy(dev, host.data(), total, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch tables");
+  fs::BatchArgs& b = p->bargs;
+  b.maps = reinterpret_cast<const CUtensorMap*>(dev + o_maps);
+  b.mem = reinterpret_cast<const fs::KArgs*>(dev + o_k0);
+  b.mem_col = b.mem;
+  p->bmem1 = reinterpret_cast<const fs::KArgs*>(dev + o_k1);
+  b.row_begin = reinterpret_cast<const long long*>(dev + o_rb);
+  b.col_begin = reinterpret_cast<const long long*>(dev + o_cb);
+  b.col_tiles = reinterpret_cast<const int*>(dev + o_t);
+  b.nm = nm;
+  b.nf1 = p->nf + 1;
+  b.row_total = rb[nm];
+  b.col_total = cb[nm];
+  b.row_grid = b.row_total;  // until tuned: one CTA per item
+  b.col_grid = b.col_total;
+  b.row_smem = rsm;
+  b.col_smem = csm;
+  p->batch = true;
+  return FS_OK;
+}
+
+// Autotuner of the batched launches: times the persistent grid sizes
+// {1, 2, 3, 4, 6, 8, 16} x SMs and one CTA per work item for each pass and
+// keeps the fastest.  Runs on the state just set (row pass from the real
+// fields, column pass on its output), which it leaves unchanged.
+cudaError_t autotune_batch(fs_plan* p) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int mult[] = {1, 2, 3, 4, 6, 8, 16};
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return e;
+  for (int kind = 0; kind < 2 && e == cudaSuccess; ++kind) {
+    long long total = kind == 0 ? p->bargs.row_total : p->bargs.col_total;
+    std::vector<long long> cand;
+    for (int mm : mult)
+      if ((long long)mm * sms < total) cand.push_back((long long)mm * sms);
+    cand.push_back(total);
+    float best = 1e30f;
+    long long best_g = total;
+    for (long long g : cand) {
+      if (kind == 0) p->bargs.row_grid = g; else p->bargs.col_grid = g;
+      float acc = 0.f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        if (kind == 1) e = launch_batch_pass(p, 1, 0, p->stream);  // fresh column input
+        if (e == cudaSuccess) e = cudaEventRecord(e0, p->stream);
+        if (e == cudaSuccess) e = launch_batch_pass(p, 1, kind, p->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0) acc += t;  // first repetition warms up
+      }
+      if (acc < best) {
+        best = acc;
+        best_g = g;
+      }
+    }
+    if (kind == 0) p->bargs.row_grid = best_g; else p->bargs.col_grid = best_g;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess) p->tuned = true;
+  return e;
+}
+
 fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc_fn alloc, fs_free_fn dealloc,
                         void* ctx, fs_plan_t* out) {
   if (!out) return fail(nullptr, FS_ERR_INVALID_ARG, "out is NULL");
@@ -603,6 +745,15 @@ fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc
     delete p;
     return s;
   }
+  if (count > 1) {
+    fs_status s = setup_batch(p);
+    if (s != FS_OK) {
+      cudaFreeHost(p->host_flag);
+      plan_free_all(p);
+      delete p;
+      return s;
+    }
+  }
   *out = p;
   return FS_OK;
 }
@@ -644,6 +795,11 @@ fs_status fs_set_fields(fs_plan_t p, const void* const* fields) {
     }
   }
   p->state = kStateReal;
+  if (p->batch && !p->tuned) {
+    cudaError_t e = autotune_batch(p);
+    if (e != cudaSuccess) return cuda_fail(p, e, "batch autotune");
+    drop_graph(p);
+  }
   return FS_OK;
 }
 
@@ -791,7 +947,17 @@ fs_status fs_step_profiled(fs_plan_t p, int64_t nsteps) {
     p->last_launches = launches;
     return FS_OK;
   }
-  for (int64_t s = 0; s < nsteps && e == cudaSuccess; ++s) {
+  for (int64_t s = 0; s < nsteps && e == cudaSuccess && p->batch; ++s) {
+    int mode = p->state == kStateReal ? 1 : 0;
+    for (int k = 0; k < 2; ++k) {
+      rec(k);
+      if (e == cudaSuccess) e = launch_batch_pass(p, mode, k, p->stream);
+      rec(k);
+      launches++;
+    }
+    p->state = kStateSpec;
+  }
+  for (int64_t s = 0; s < nsteps && e == cudaSuccess && !p->batch; ++s) {
     int mode = p->state == kStateReal ? 1 : 0;
     for (const Member& m : p->members) {
       fs::KArgs a = make_args(p, m, mode);
@@ -825,7 +991,7 @@ fs_status fs_profile_read(fs_plan_t p, double* ms_per_pass, int64_t* launches_pe
   }
   p->ev_used = 0;
   if (e != cudaSuccess) return cuda_fail(p, e, "fs_profile_read");
-  int used = p->fd ? 1 : pass_kinds(p->members[0]);
+  int used = p->fd ? 1 : (p->batch ? 2 : pass_kinds(p->members[0]));
   int n = used < npass_max ? used : npass_max;
   for (int i = 0; i < n; ++i) {
     ms_per_pass[i] = ms[i];
@@ -833,6 +999,17 @@ fs_status fs_profile_read(fs_plan_t p, double* ms_per_pass, int64_t* launches_pe
   }
   *npass = n;
   return read_flag(p);
+}
+
+fs_status fs_batch_schedule(fs_plan_t p, int64_t* row_grid, int64_t* col_grid, int64_t* row_items,
+                            int64_t* col_items) {
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  if (!p->batch) return fail(p, FS_ERR_INVALID_ARG, "not a batched plan");
+  if (row_grid) *row_grid = p->bargs.row_grid;
+  if (col_grid) *col_grid = p->bargs.col_grid;
+  if (row_items) *row_items = p->bargs.row_total;
+  if (col_items) *col_items = p->bargs.col_total;
+  return FS_OK;
 }
 
 fs_status fs_workspace_bytes(fs_plan_t p, size_t* bytes) {

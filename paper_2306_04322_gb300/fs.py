@@ -81,6 +81,7 @@ def lib(build_if_missing: bool = False):
         "fs_step_profiled": [plan, ctypes.c_int64],
         "fs_profile_read": [plan, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                             ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+        "fs_batch_schedule": [plan] + [ctypes.POINTER(ctypes.c_int64)] * 4,
         "fs_workspace_bytes": [plan, ctypes.POINTER(ctypes.c_size_t)],
         "fs_last_launch_count": [plan, ctypes.POINTER(ctypes.c_int64)],
         "fs_destroy": [plan],
@@ -219,6 +220,13 @@ def fs_profile_read(plan, npass_max: int = 8):
     n = ctypes.c_int()
     _check(lib().fs_profile_read(plan, ms, cnt, npass_max, ctypes.byref(n)), plan)
     return list(ms[:n.value]), list(cnt[:n.value])
+
+
+def fs_batch_schedule(plan):
+    """(row grid, column grid, row items, column items) of a batched plan."""
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().fs_batch_schedule(plan, *[ctypes.byref(x) for x in v]), plan)
+    return tuple(x.value for x in v)
 
 
 def fs_workspace_bytes(plan) -> int:
