@@ -23,6 +23,7 @@ struct Coef {
   T two_rho2, ca, dcab, rho2dcab, cab, w, four_alpha, Ldt;  // pointwise stage
   T Mdt, Mdtkc, Ldtke, scale;                               // k-space update
   T idx2, idy2, idz2, kc, ke, dtM, dtL;                     // explicit FD scheme
+  T dt;                                                     // adjoint
 };
 
 // Arguments of one pass over one simulation (passed by value).  Array
@@ -30,6 +31,7 @@ struct Coef {
 struct KArgs {
   void* spec;              // packed half spectra: slots of slot_stride complex values
   void* real;              // real fields: nf arrays of npts values
+  const void* aux;         // adjoint: the state u the step is linearised at (real, nf arrays)
   const void* tw_row;      // pass tables of the x line FFT (L = nx/2)
   const void* tw_col;      // pass tables of the y line FFT (L = ny)
   const void* tw_z;        // pass tables of the z line FFT (L = nz, 3D)
@@ -46,6 +48,7 @@ struct KArgs {
   double scale;            // k-space scale 1 / (2 N)
   double inv_npts;         // 1 / N
   const double* csum;      // FP64 sum of c carried for the k = 0 mode (NULL: off)
+  double* acc;             // FP64 accumulators of the free-energy diagnostic (2 + p)
   int* flag;               // sticky error bits (FS_FLAG_*)
   Coef<float> cf;          // coefficients, FP32 copy
   Coef<double> cd;         // coefficients, FP64 copy
@@ -61,6 +64,15 @@ cudaError_t row_launch_f32(const KArgs& a, cudaStream_t s);
 cudaError_t row_launch_f64(const KArgs& a, cudaStream_t s);
 cudaError_t col_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
 cudaError_t col_launch_f64(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
+// Free-energy diagnostic, 2D (row pass mode 3 does the chemical sum and the
+// x transforms): y transforms and sums of w K2 |phi^|^2 per field.
+cudaError_t energy_col_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
+cudaError_t energy_col_launch_f64(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
+// Adjoint of one 2D step (fs_adjoint_f32.cu / fs_adjoint_f64.cu): spec = the
+// 3 nf adjoint slots, real = lam' in / lambda out, aux = u, acc[0..3] += the
+// raw sensitivity sums; tm = tensor map over the adjoint slots.
+cudaError_t adjoint_launch_f32(const KArgs& a, const CUtensorMap& tm, void* lam_out, cudaStream_t s);
+cudaError_t adjoint_launch_f64(const KArgs& a, const CUtensorMap& tm, void* lam_out, cudaStream_t s);
 // Columns per CTA of the 2D column pass for this grid (the TMA box width).
 int col_tile_width(bool f64, int nx, int ny);
 // 3D passes (fs_k3d_f32.cu / fs_k3d_f64.cu): y transform of nslots slots of

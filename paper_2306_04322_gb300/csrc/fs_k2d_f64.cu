@@ -9,4 +9,7 @@ cudaError_t col_launch_f64(const KArgs& a, const CUtensorMap& tm, cudaStream_t s
 cudaError_t sum_launch_f64(const void* x, long long n, double* out, cudaStream_t s) {
   return sum_launch_t<double>(x, n, out, s);
 }
+cudaError_t energy_col_launch_f64(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+  return energy_col_launch_t<double>(a, tm, s);
+}
 }  // namespace fs

@@ -50,6 +50,34 @@ cudaError_t col_launch_n(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) 
   return cudaGetLastError();
 }
 
+template <typename T, int NY>
+cudaError_t energy_col_launch_n(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+  using Cfg = ColCfg<T, NY>;
+  const int tk = col_tk_n<T, NY>(a.nx);
+  size_t smem = Cfg::HEAD + (size_t)Cfg::TROWS * tk * sizeof(cplx<T>);
+  static unsigned done = 0;
+  cudaError_t e = allow_big_smem(fs_energy_col_kernel<T, NY>, &done);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)(a.nx / 2 / tk), (unsigned)a.nf);
+  fs_energy_col_kernel<T, NY><<<grid, (unsigned)(tk * Cfg::TPL), smem, s>>>(a, tm);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t energy_col_launch_t(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+  switch (a.ny) {
+    case 8: return energy_col_launch_n<T, 8>(a, tm, s);
+    case 16: return energy_col_launch_n<T, 16>(a, tm, s);
+    case 32: return energy_col_launch_n<T, 32>(a, tm, s);
+    case 64: return energy_col_launch_n<T, 64>(a, tm, s);
+    case 128: return energy_col_launch_n<T, 128>(a, tm, s);
+    case 256: return energy_col_launch_n<T, 256>(a, tm, s);
+    case 512: return energy_col_launch_n<T, 512>(a, tm, s);
+    case 1024: return energy_col_launch_n<T, 1024>(a, tm, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
 cudaError_t row_launch_t(const KArgs& a, cudaStream_t s) {
   switch (a.nx) {

@@ -87,6 +87,8 @@ __device__ __forceinline__ bool finite_val(T x) {
 // mode 0: step, previous state in spec slots 0..nf-1 (y-inverted spectra)
 // mode 1: step, previous state in the real fields
 // mode 2: inverse only: spec slots 0..nf-1 -> real fields
+// mode 3: free-energy diagnostic: real fields in, sum of f_chem into acc[0],
+//         2 x^(phi) of every field into spec slots 0..nf-1
 // Outputs of a step: spec slot 0 = 2 x^(c), slots 1..p = 2 x^(g_i),
 // slot nf = 2 x^(df/dc) (x-spectra scaled by 2; the factor is folded into
 // the k-space scale).
@@ -145,7 +147,8 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
     const uint32_t bytes = (uint32_t)(L * sizeof(C));
     mbar_arrive_expect_tx(bar, bytes * Reff * nf);
     for (int f = 0; f < nf; ++f) {
-      const C* src = (a.mode == 1) ? realc + f * half_stride + row0 * L : spec + f * a.slot_stride + row0 * L;
+      const bool from_real = (a.mode == 1 || a.mode == 3);
+      const C* src = from_real ? realc + f * half_stride + row0 * L : spec + f * a.slot_stride + row0 * L;
       for (int r = 0; r < Reff; ++r) bulk_g2s(slot(f, r), src + r * L, bytes, bar);
     }
   }
@@ -156,7 +159,7 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
   }
 
   // phase 1: inverse x transforms (real pairs x[2j], x[2j+1] back into the slots)
-  if (a.mode != 1 && w < nf) {
+  if ((a.mode == 0 || a.mode == 2) && w < nf) {
     C* s = slot(w, g);
     auto st = [s](int i, C v) { s[pad32(i)] = v; };
     auto ld = [s](int i) { return s[pad32(i)]; };
@@ -191,7 +194,39 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
 
   // phase 2: pointwise derivative stage, all threads over all R * L pairs
   bool bad = false;
-  {
+  if (a.mode == 3) {
+    // chemical free energy f_chem = rho2 (c-ca)^2 (1-h) + rho2 (cb-c)^2 h + w g
+    const Coef<T>& k = coef<T>(a);
+    const T rho2 = k.two_rho2 * T(0.5), cb = k.ca + k.dcab, alpha = k.four_alpha * T(0.25);
+    const Pointwise<T> pw(a);
+    const int p = nf - 1;
+    double sum = 0.0;
+    for (int idx = threadIdx.x; idx < Reff * L; idx += blockDim.x) {
+      const int r = idx / L, i0 = idx % L;
+      const C c = slot(0, r)[i0];
+      T part[2];
+      const T cc[2] = {c.x, c.y};
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+        T h = T(0), g = T(0), s2 = T(0), s4 = T(0);
+        for (int i = 0; i < p; ++i) {
+          const C e2 = slot(1 + i, r)[i0];
+          const T e = h2 ? e2.y : e2.x;
+          h += pw.hpoly(e);
+          g += e * e * (T(1) - e) * (T(1) - e);
+          s2 += e * e;
+          s4 += e * e * e * e;
+        }
+        g += alpha * (s2 * s2 - s4);
+        const T da = cc[h2] - k.ca, db = cb - cc[h2];
+        part[h2] = rho2 * da * da * (T(1) - h) + rho2 * db * db * h + k.w * g;
+      }
+      sum += (double)part[0] + (double)part[1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    if (lane == 0) atomicAdd(&a.acc[0], sum);
+  } else {
     const Pointwise<T> pw(a);
     const int p = nf - 1;
     for (int idx = threadIdx.x; idx < Reff * L; idx += blockDim.x) {
@@ -216,6 +251,7 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
     }
   }
   __syncthreads();
+  if (a.mode == 3 && w == nf) return true;  // the diagnostic transforms nf slots
 
   // phase 3: forward x transform of slot w (c, g_1..g_p, df/dc), packed half
   // spectra scaled by 2, straight to global memory
@@ -436,6 +472,82 @@ __device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap
 #pragma unroll
   for (int m = 0; m < E; ++m) S[(long long)(t + TPL * m) * Lh] = v[m];
   return true;
+}
+
+// Free-energy diagnostic, gradient terms (Eq. fe through Parseval): forward
+// y transform of slot g (= field g) and the sum of w(kx) K2 |phi^|^2 over the
+// tile, w = 2 for 0 < kx < nx/2 (the conjugate half is not stored), 1 for
+// the separated kx = 0 and kx = nx/2 columns; FP64 atomics into acc[1 + g].
+template <typename T, int NY>
+__global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
+    fs_energy_col_kernel(KArgs a, const __grid_constant__ CUtensorMap tmap) {
+  using C = cplx<T>;
+  using Cfg = ColCfg<T, NY>;
+  constexpr int E = Cfg::E, TPL = Cfg::TPL, BH = Cfg::BH, TROWS = Cfg::TROWS, LOGE = Cfg::LOGE;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  C* twc = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);
+  T* k2yt = reinterpret_cast<T*>(smem_raw + Cfg::BAR_BYTES + Cfg::TW_BYTES);
+  C* tile = reinterpret_cast<C*>(smem_raw + Cfg::HEAD);
+  const int tk = blockDim.x / TPL;
+  const int j = threadIdx.x % tk, t = threadIdx.x / tk;
+  const int Lh = a.nx / 2;
+  const int kx0 = blockIdx.x * tk, kx = kx0 + j, g = blockIdx.y;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(bar, (uint32_t)(NY * tk * sizeof(C)));
+    const int cx = kx0 * (int)(sizeof(C) / 8);
+    for (int y0 = 0; y0 < NY; y0 += BH) tma_load_3d(tile + y0 * tk, &tmap, cx, y0, g, bar);
+  }
+  copy_to_smem(twc, reinterpret_cast<const C*>(a.tw_col), Cfg::TWS);
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) k2yt[i] = reinterpret_cast<const T*>(a.k2y)[i];
+  __syncthreads();
+  if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
+    if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
+    mbar_wait_bounded(bar, 0, kWaitPolls);
+    return;
+  }
+  C v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = tile[(t + TPL * m) * tk + j];
+  {
+    C* tl = tile + j;
+    auto st = [tl, tk](int q, C x) { tl[(q + (q >> LOGE)) * tk] = x; };
+    auto ld = [tl, tk](int q) { return tl[(q + (q >> LOGE)) * tk]; };
+    line_fft<NY, E, -1>(v, t, twc, st, ld, []() { __syncthreads(); });
+  }
+  const T* k2xt = reinterpret_cast<const T*>(a.k2x);
+  const double kx2 = (double)k2xt[kx], kxn2 = (double)k2xt[Lh];
+  double sum = 0.0;
+  const bool special = (kx0 == 0);
+  if (special) {
+    __syncthreads();
+    if (j == 0) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) tile[(t + TPL * m) * tk] = v[m];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int ky = t + TPL * m;
+    const double ky2 = (double)k2yt[ky];
+    if (special && j == 0) {
+      const C pz = cconj(tile[((NY - ky) & (NY - 1)) * tk]);
+      const C A = cscale(cadd(v[m], pz), T(0.5)), B = cscale(mul_i<-1>(csub(v[m], pz)), T(0.5));
+      sum += (kx2 + ky2) * ((double)A.x * A.x + (double)A.y * A.y);
+      sum += (kxn2 + ky2) * ((double)B.x * B.x + (double)B.y * B.y);
+    } else {
+      sum += 2.0 * (kx2 + ky2) * ((double)v[m].x * v[m].x + (double)v[m].y * v[m].y);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&a.acc[1 + g], sum);
 }
 
 template <typename T, int NY>

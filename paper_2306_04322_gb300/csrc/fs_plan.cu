@@ -39,6 +39,12 @@ struct Member {
   CUtensorMap tmap_col;  // [slot * nz + z][y][kx] tiles of the 2D column pass / 3D y passes
   CUtensorMap tmap_z;    // [slot][z][y][kx] z lines of the 3D z step
   int fd_cur = 0;        // explicit FD: 0 state in `real`, 1 state in `spec` (as real fields)
+  // adjoint workspace (allocated on first use)
+  void* aspec = nullptr;  // 3 nf packed half-spectrum slots
+  void* alam = nullptr;   // lam' in (nf real fields)
+  void* au = nullptr;     // u (nf real fields)
+  void* aout = nullptr;   // lambda out (nf real fields)
+  CUtensorMap tmap_adj;
 };
 
 }  // namespace
@@ -60,6 +66,7 @@ struct fs_plan {
   std::vector<void*> blocks;
   size_t ws_bytes = 0;
   int* flag = nullptr;
+  double* acc = nullptr;     // diagnostic accumulators (device)
   int* host_flag = nullptr;  // pinned
   int state = kStateNone;
   cudaGraphExec_t gexec = nullptr;
@@ -207,6 +214,7 @@ void fill_coef(fs::Coef<T>& k, const fs_params& q, double scale) {
   k.ke = (T)q.kappa_eta;
   k.dtM = (T)(q.dt * q.M);
   k.dtL = (T)(q.dt * q.L);
+  k.dt = (T)q.dt;
   k.two_rho2 = (T)(2.0 * q.rho2);
   k.ca = (T)q.c_alpha;
   k.dcab = (T)(q.c_beta - q.c_alpha);
@@ -255,6 +263,7 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   a.inv_npts = 1.0 / (double)m.npts;
   a.csum = p->f64 ? nullptr : m.csum;
   a.flag = p->flag;
+  a.acc = p->acc;
   fill_coef(a.cd, m.prm, a.scale);
   fill_coef(a.cf, m.prm, a.scale);
   return a;
@@ -721,7 +730,8 @@ fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc
     m.k2x = tb;  // the rest of the table pointers are set by upload_tables
   }
   p->flag = (int*)plan_alloc(p, 256);
-  if (!p->flag) {
+  p->acc = (double*)plan_alloc(p, 256);
+  if (!p->flag || !p->acc) {
     plan_free_all(p);
     delete p;
     return fail(nullptr, FS_ERR_OOM, "device workspace allocation failed");
@@ -898,20 +908,102 @@ fs_status fs_set_stream(fs_plan_t p, void* stream) {
 }
 
 fs_status fs_free_energy(fs_plan_t p, double* F, double* parts) {
-  (void)parts;
   if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
   if (!F) return fail(p, FS_ERR_INVALID_ARG, "F is NULL");
-  return fail(p, FS_ERR_UNSUPPORTED, "fs_free_energy is not built in this library version");
+  if (p->state == kStateNone) return fail(p, FS_ERR_STATE, "fs_free_energy before fs_set_fields");
+  const Member& m = p->members[0];
+  if (p->members.size() != 1 || p->fd || m.prm.ndim != 2)
+    return fail(p, FS_ERR_UNSUPPORTED, "fs_free_energy is built for single 2D semi-implicit FS plans");
+  cudaError_t e = cudaSuccess;
+  if (p->state == kStateSpec) {
+    e = launch_row(p, make_args(p, m, 2), p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "inverse row pass");
+  }
+  p->state = kStateReal;  // the diagnostic overwrites the spectra
+  const int nparts = 2 + m.prm.p;
+  e = cudaMemsetAsync(p->acc, 0, sizeof(double) * nparts, p->stream);
+  fs::KArgs a = make_args(p, m, 3);
+  if (e == cudaSuccess) e = launch_row(p, a, p->stream);
+  if (e == cudaSuccess)
+    e = p->f64 ? fs::energy_col_launch_f64(a, m.tmap_col, p->stream) : fs::energy_col_launch_f32(a, m.tmap_col, p->stream);
+  double h[8] = {0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, p->acc, sizeof(double) * nparts, cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(p, e, "fs_free_energy");
+  double dV = 1.0;
+  for (int d = 0; d < m.prm.ndim; ++d) dV *= m.prm.dx[d];
+  const double N = (double)m.npts;
+  double total = h[0] * dV;
+  if (parts) parts[0] = h[0] * dV;
+  for (int f = 0; f < 1 + m.prm.p; ++f) {
+    const double kap = f == 0 ? m.prm.kappa_c : m.prm.kappa_eta;
+    const double term = 0.5 * kap * (h[1 + f] / (4.0 * N)) * dV;  // Parseval; spectra carry a factor 2
+    if (parts) parts[1 + f] = term;
+    total += term;
+  }
+  *F = total;
+  return read_flag(p);
 }
 
 fs_status fs_step_adjoint(fs_plan_t p, const void* const* u, const void* const* lam_in, void* const* lam_out,
                           double grad[4]) {
-  (void)u;
-  (void)lam_in;
-  (void)lam_out;
-  (void)grad;
   if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
-  return fail(p, FS_ERR_UNSUPPORTED, "fs_step_adjoint is not built in this library version");
+  if (!u || !lam_in || !lam_out) return fail(p, FS_ERR_INVALID_ARG, "field pointer array is NULL");
+  Member& m = p->members[0];
+  if (p->members.size() != 1 || p->fd || m.prm.ndim != 2)
+    return fail(p, FS_ERR_UNSUPPORTED, "fs_step_adjoint is built for single 2D semi-implicit FS plans");
+  const size_t rs = p->f64 ? sizeof(double) : sizeof(float), cs = 2 * rs;
+  const int nf = p->nf;
+  if (!m.aspec) {
+    m.aspec = plan_alloc(p, (size_t)3 * nf * m.slot_stride * cs);
+    m.alam = plan_alloc(p, (size_t)nf * m.npts * rs);
+    m.au = plan_alloc(p, (size_t)nf * m.npts * rs);
+    m.aout = plan_alloc(p, (size_t)nf * m.npts * rs);
+    if (!m.aspec || !m.alam || !m.au || !m.aout) return fail(p, FS_ERR_OOM, "adjoint workspace allocation failed");
+    EncodeTiledFn enc = encode_tiled();
+    const int units = p->f64 ? 2 : 1, nx = m.prm.n[0], ny = m.prm.n[1];
+    const int tk = fs::col_tile_width(p->f64, nx, ny);
+    const cuuint64_t W = (cuuint64_t)(nx / 2) * units;
+    cuuint64_t dims[3] = {W, (cuuint64_t)ny, (cuuint64_t)(3 * nf)};
+    cuuint64_t strides[2] = {W * 8, W * 8 * ny};
+    cuuint32_t box[3] = {(cuuint32_t)(tk * units), (cuuint32_t)(ny < 256 ? ny : 256), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    if (!enc || enc(&m.tmap_adj, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, m.aspec, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return fail(p, FS_ERR_CUDA, "adjoint tensor map");
+  }
+  cudaError_t e = cudaSuccess;
+  for (int f = 0; f < nf && e == cudaSuccess; ++f) {
+    if (!u[f] || !lam_in[f] || !lam_out[f]) return fail(p, FS_ERR_INVALID_ARG, "field pointer is NULL");
+    e = cudaMemcpyAsync((char*)m.au + f * m.npts * rs, u[f], m.npts * rs, cudaMemcpyDefault, p->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((char*)m.alam + f * m.npts * rs, lam_in[f], m.npts * rs, cudaMemcpyDefault, p->stream);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->acc, 0, sizeof(double) * 4, p->stream);
+  fs::KArgs a = make_args(p, m, 0);
+  a.spec = m.aspec;
+  a.slot_stride = m.slot_stride;
+  a.real = m.alam;
+  a.aux = m.au;
+  if (e == cudaSuccess)
+    e = p->f64 ? fs::adjoint_launch_f64(a, m.tmap_adj, m.aout, p->stream)
+               : fs::adjoint_launch_f32(a, m.tmap_adj, m.aout, p->stream);
+  for (int f = 0; f < nf && e == cudaSuccess; ++f)
+    e = cudaMemcpyAsync(lam_out[f], (char*)m.aout + f * m.npts * rs, m.npts * rs, cudaMemcpyDefault, p->stream);
+  if (e != cudaSuccess) return cuda_fail(p, e, "fs_step_adjoint");
+  p->last_launches = 3;
+  if (grad) {
+    double h[4];
+    e = cudaMemcpyAsync(h, p->acc, sizeof(h), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "fs_step_adjoint sensitivities");
+    // Parseval 1/N, and both spectra carry the factor 2 of the packed x transform
+    const double norm = 1.0 / (4.0 * (double)m.npts);
+    for (int q = 0; q < 4; ++q) grad[q] += h[q] * norm;
+    return read_flag(p);
+  }
+  return FS_OK;
 }
 
 fs_status fs_step_profiled(fs_plan_t p, int64_t nsteps) {

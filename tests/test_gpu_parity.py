@@ -184,3 +184,33 @@ def test_set_params_changes_dt(F, O):
     plan.step(40)
     ref, _ = O.step(pr2, f0, 40)
     assert rel_linf(plan.get_fields().cpu().numpy(), ref) <= 1e-11
+
+
+@pytest.mark.parametrize("precision,n,p,tol", [("f64", (64, 64), 1, 1e-12), ("f64", (128, 32), 3, 1e-12),
+                                               ("f32", (256, 256), 2, 1e-5)])
+def test_free_energy_matches_oracle(F, O, precision, n, p, tol):
+    """Eq. (fe) diagnostic: chemical and gradient parts against the oracle,
+    before and after steps (spectral state materialised first)."""
+    import torch
+    pr = I.Problem(n=n, dx=(1.0, 0.5), p=p)
+    pr.dt = 5.0 * I.fd_stable_dt(pr)
+    f0 = I.noise_fields(pr, seed=14, amp=0.1)
+    dt = torch.float64 if precision == "f64" else torch.float32
+    plan = F.Plan(pr, precision)
+    plan.set_fields(torch.tensor(f0, dtype=dt, device="cuda"))
+    E0, parts0 = plan.free_energy()
+    f_in = f0.astype(np.float32).astype(np.float64) if precision == "f32" else f0
+    Fo, po = O.free_energy(pr, f_in, parts=True)
+    assert abs(E0 - Fo) <= tol * abs(Fo)
+    assert np.allclose(parts0, po, rtol=tol * 10, atol=tol * abs(Fo))
+    plan.step(10)
+    E1, _ = plan.free_energy()
+    g = plan.get_fields().double().cpu().numpy()
+    assert abs(E1 - O.free_energy(pr, g)) <= tol * abs(Fo)
+    assert E1 < E0
+    # the diagnostic leaves the state usable: stepping on gives the same as without it
+    plan.step(5)
+    h = plan.get_fields().double().cpu().numpy()
+    plan.close()
+    ref, _ = O.step(pr, g, 5)
+    assert rel_linf(h, ref) <= (1e-12 if precision == "f64" else 2e-5)
