@@ -169,6 +169,27 @@ fs_status fs_profile_read(fs_plan_t plan, double* ms_per_pass, int64_t* launches
 fs_status fs_batch_schedule(fs_plan_t plan, int64_t* row_grid, int64_t* col_grid, int64_t* row_items,
                             int64_t* col_items);
 
+/* Allocation-free 2D step, for callers that cannot allocate device memory
+ * (the paper has no counterpart; it is a deployment convenience).  Advances
+ * `fields` -- one device array of (1 + p) * nx * ny values in the plan layout
+ * (c, eta_1 .. eta_p, x fastest) -- by nsteps semi-implicit FS steps in
+ * place, with the same kernels and results as a plan.  All intermediates
+ * live in one fixed file-scope device array of 2,228,480 bytes that every GPU
+ * loading the library holds until the process exits; the call makes no
+ * cudaMalloc / cudaFree and no host heap allocation.
+ *   - Limits: 2D, each axis a power of two in [8, 1024], nx * ny <= 65536,
+ *     p <= 2, precision FS_F64 or FS_F32, scheme FS_SCHEME_SEMI_IMPLICIT_FS.
+ *     Larger requests return FS_ERR_UNSUPPORTED before any CUDA call; other
+ *     bad arguments return FS_ERR_INVALID_ARG.  fs_last_error() is not set.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call shares the array and overwrites it.  Calls whose work
+ *     overlaps on the GPU (several streams or host threads at once) race;
+ *     serialise them.
+ *   - Synchronises `stream` (a cudaStream_t) before returning the status. */
+fs_status fs_step2d_static(const fs_params* prm, void* fields, int64_t nsteps, void* stream);
+
 /* Device bytes owned by the plan. */
 fs_status fs_workspace_bytes(fs_plan_t plan, size_t* bytes);
 

@@ -85,6 +85,7 @@ def lib(build_if_missing: bool = False):
         "fs_workspace_bytes": [plan, ctypes.POINTER(ctypes.c_size_t)],
         "fs_last_launch_count": [plan, ctypes.POINTER(ctypes.c_int64)],
         "fs_destroy": [plan],
+        "fs_step2d_static": [P, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -243,6 +244,13 @@ def fs_last_launch_count(plan) -> int:
 
 def fs_destroy(plan):
     _check(lib().fs_destroy(plan))
+
+
+def fs_step2d_static(params: fs_params, fields, nsteps: int, stream=None) -> int:
+    """Allocation-free 2D step on one contiguous device array of all fields;
+    returns the status code (no exception, the call sets no error text)."""
+    s = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    return lib().fs_step2d_static(ctypes.byref(params), ctypes.c_void_p(_ptr(fields)), int(nsteps), s)
 
 
 def fs_version() -> str:
