@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the 3D and ensemble measurements")
     return ap.parse_args()
 
 
@@ -168,6 +169,88 @@ def time_gpu(precision: str, steps: int, warmup: int, device: int):
     plan.close()
     return {"total_ms": total_ms, "kern_ms": kern_ms, "kern_cnt": kern_cnt, "launches": launches,
             "workspace_bytes": ws, "npts": pr.npoints}
+
+
+def time_plan(probs, precision: str, steps: int, warmup: int, device: int, flush_mb: int = 512):
+    """Device time of `steps` steps of a plan (a list of problems = ensemble),
+    L2 flushed before every timed step; per-pass times from the plan."""
+    import torch
+    from paper_2306_04322_gb300 import fs, inputs as I
+    dtype = torch.float64 if precision == "f64" else torch.float32
+    batch = isinstance(probs, list)
+    plist = probs if batch else [probs]
+    fields = [torch.tensor(I.noise_fields(p, seed=i), dtype=dtype, device=f"cuda:{device}")
+              for i, p in enumerate(plist)]
+    plan = fs.Plan(plist if batch else plist[0], precision)
+    plan.set_fields(fields if batch else fields[0])
+    sched = fs.fs_batch_schedule(plan.h) if batch else None
+    flush = torch.empty(flush_mb * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{device}")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush.zero_()
+        fs.fs_step_async(plan.h, 1)
+    fs.fs_profile_read(plan.h)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        fs.fs_step_profiled(plan.h, 1)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    kern_ms, kern_cnt = fs.fs_profile_read(plan.h)
+    ws = plan.workspace_bytes
+    plan.close()
+    del fields, flush
+    npts = sum(p.npoints for p in plist)
+    return {"total_ms": total_ms, "kern_ms": kern_ms, "kern_cnt": kern_cnt, "launches": sum(kern_cnt),
+            "workspace_bytes": ws, "npts": npts, "schedule": sched}
+
+
+def roofline_entry(names, alg_bytes, r, peak, peak_kind):
+    avg_ms = [m / max(c, 1) for m, c in zip(r["kern_ms"], r["kern_cnt"])]
+    dom = max(range(len(avg_ms)), key=lambda i: r["kern_ms"][i])
+    achieved = alg_bytes[dom] / (avg_ms[dom] / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes[dom],
+            "avg_launch_ms": avg_ms[dom],
+            "kernels": {n: {"avg_ms": a, "launches": c, "share": m / max(sum(r["kern_ms"]), 1e-30),
+                            "alg_GBps": b / (a / 1e3) / 1e9 if a > 0 else None}
+                        for n, a, c, m, b in zip(names, avg_ms, r["kern_cnt"], r["kern_ms"], alg_bytes)}}
+
+
+def extras(steps: int, warmup: int, device: int, peak, peak_kind):
+    """3D 256^3 (p = 2, FP32) and the 512-member ensemble (FP32): throughput
+    and per-pass rooflines, reported beside the headline."""
+    from paper_2306_04322_gb300 import inputs as I
+    out = {}
+    pr = I.Problem(n=(256, 256, 256), p=P)
+    pr.dt = 6.0 * I.fd_stable_dt(pr)
+    k = max(3, min(steps, 20))
+    r = time_plan(pr, "f32", k, min(warmup, 3), device)
+    nf, s, N = 1 + P, 4, r["npts"]
+    alg = [(2 * nf + 1) * N * s, 2 * (nf + 1) * N * s, (2 * nf + 1) * N * s, 2 * nf * N * s]
+    out["3d_256_p2_f32"] = {"value": N * k / (r["total_ms"] / 1e3), "unit": UNIT, "steps": k,
+                            "ms_per_step": r["total_ms"] / k, "dt": pr.dt, "launches": r["launches"],
+                            "workspace_bytes": r["workspace_bytes"],
+                            "roofline": roofline_entry(["x_pass(fs_row_kernel)", "fs_ypass_kernel<-1>",
+                                                        "fs_zstep_kernel", "fs_ypass_kernel<+1>"],
+                                                       alg, r, peak, peak_kind)}
+    probs = I.batch_problems(512, seed=0)
+    kb = max(3, min(steps, 10))
+    r = time_plan(probs, "f32", kb, min(warmup, 3), device)
+    N = r["npts"]
+    alg = [(2 * nf + 1) * N * s, (2 * nf + 1) * N * s]
+    out["batched_512_f32"] = {"value": N * kb / (r["total_ms"] / 1e3), "unit": UNIT, "steps": kb,
+                              "ms_per_step": r["total_ms"] / kb, "members": 512, "points": N,
+                              "launches": r["launches"], "schedule": {"row_grid": r["schedule"][0],
+                                                                       "col_grid": r["schedule"][1],
+                                                                       "row_items": r["schedule"][2],
+                                                                       "col_items": r["schedule"][3]},
+                              "roofline": roofline_entry(["fs_row_batch_kernel", "fs_col_batch_kernel"],
+                                                         alg, r, peak, peak_kind)}
+    return out
 
 
 def time_e2e(steps: int, warmup: int, device: int):
@@ -294,6 +377,9 @@ def main():
     barrier()
     e2e = time_e2e(args.steps, args.warmup, local)
     barrier()
+    peak, peak_kind = load_peaks()
+    ext = {} if args.no_extras else extras(args.steps, args.warmup, local, peak, peak_kind)
+    barrier()
 
     t32 = max_over_ranks(r32["total_ms"]) / 1e3
     t64 = max_over_ranks(r64["total_ms"]) / 1e3
@@ -305,7 +391,6 @@ def main():
             dist.destroy_process_group()
         return
 
-    peak, peak_kind = load_peaks()
     s = 4
     nf = 1 + P
     names = ["fs_row_kernel", "fs_col_kernel"]
@@ -340,6 +425,7 @@ def main():
         "fp64": {"value": world * npts * args.steps / t64, "unit": UNIT, "ms_per_step": t64 * 1e3 / args.steps,
                  "kernels_ms": r64["kern_ms"], "launches": r64["launches"]},
     }
+    line.update(ext)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
