@@ -158,132 +158,141 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
     return false;
   }
 
-  // phase 1: inverse x transforms (real pairs x[2j], x[2j+1] back into the slots)
-  if ((a.mode == 0 || a.mode == 2) && w < nf) {
-    C* s = slot(w, g);
-    auto st = [s](int i, C v) { s[pad32(i)] = v; };
-    auto ld = [s](int i) { return s[pad32(i)]; };
-    C v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int k = t + TPL * m;
-      const C pk = s[k];
-      if (k == 0) {
-        v[m] = mk<C>(pk.x + pk.y, pk.x - pk.y);
-      } else {
-        const C pm = cconj(s[L - k]);
-        const C A = cadd(pk, pm), B = csub(pk, pm);
-        v[m] = cadd(A, mul_i<1>(mul_tw<1>(B, __ldg(&twh[k]))));
-      }
-    }
-    line_fft<L, E, 1>(v, t, twr, st, ld, wsync);
-    if (a.mode == 2) {
-      C* dst = realc + w * half_stride + row * L;
-      if (active) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) dst[t + TPL * m] = v[m];
-      }
-    } else {
-      wsync();
-#pragma unroll
-      for (int m = 0; m < E; ++m) s[t + TPL * m] = v[m];
-    }
-  }
-  if (a.mode == 2) return true;
-  __syncthreads();
-
-  // phase 2: pointwise derivative stage, all threads over all R * L pairs
+  // Both transform phases share one FFT call site (small instruction
+  // footprint); the inverse is computed as conj(FFT(conj(.))).
+  //   phase 1 (ph = 0): warp f < nf, inverse x transform of field f (modes 0, 2)
+  //   phase 2         : pointwise stage, all threads
+  //   phase 3 (ph = 1): warp o <= nf, forward x transform of slot o
   bool bad = false;
-  if (a.mode == 3) {
-    // chemical free energy f_chem = rho2 (c-ca)^2 (1-h) + rho2 (cb-c)^2 h + w g
-    const Coef<T>& k = coef<T>(a);
-    const T rho2 = k.two_rho2 * T(0.5), cb = k.ca + k.dcab, alpha = k.four_alpha * T(0.25);
-    const Pointwise<T> pw(a);
-    const int p = nf - 1;
-    double sum = 0.0;
-    for (int idx = threadIdx.x; idx < Reff * L; idx += blockDim.x) {
-      const int r = idx / L, i0 = idx % L;
-      const C c = slot(0, r)[i0];
-      T part[2];
-      const T cc[2] = {c.x, c.y};
+  for (int ph = 0; ph < 2; ++ph) {
+    const bool inv = (ph == 0);
+    const bool busy = inv ? ((a.mode == 0 || a.mode == 2) && w < nf) : !(a.mode == 3 && w == nf);
+    if (busy) {
+      C* s = slot(w, g);
+      auto st = [s](int i, C v) { s[pad32(i)] = v; };
+      auto ld = [s](int i) { return s[pad32(i)]; };
+      C v[E];
+      if (inv) {
+        // half-length complex sequence of the real row from its packed half
+        // spectrum (conjugated for the conj-FFT-conj inverse)
 #pragma unroll
-      for (int h2 = 0; h2 < 2; ++h2) {
-        T h = T(0), g = T(0), s2 = T(0), s4 = T(0);
-        for (int i = 0; i < p; ++i) {
-          const C e2 = slot(1 + i, r)[i0];
-          const T e = h2 ? e2.y : e2.x;
-          h += pw.hpoly(e);
-          g += e * e * (T(1) - e) * (T(1) - e);
-          s2 += e * e;
-          s4 += e * e * e * e;
+        for (int m = 0; m < E; ++m) {
+          const int k = t + TPL * m;
+          const C pk = s[k];
+          C z;
+          if (k == 0) {
+            z = mk<C>(pk.x + pk.y, pk.x - pk.y);
+          } else {
+            const C pm = cconj(s[L - k]);
+            const C A = cadd(pk, pm), B = csub(pk, pm);
+            z = cadd(A, mul_i<1>(mul_tw<1>(B, __ldg(&twh[k]))));
+          }
+          v[m] = cconj(z);
         }
-        g += alpha * (s2 * s2 - s4);
-        const T da = cc[h2] - k.ca, db = cb - cc[h2];
-        part[h2] = rho2 * da * da * (T(1) - h) + rho2 * db * db * h + k.w * g;
+      } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = s[t + TPL * m];
       }
-      sum += (double)part[0] + (double)part[1];
-    }
+      line_fft<L, E, -1>(v, t, twr, st, ld, wsync);
+      if (inv) {
+        if (a.mode == 2) {
+          C* dst = realc + w * half_stride + row * L;
+          if (active) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
-    if (lane == 0) atomicAdd(&a.acc[0], sum);
-  } else {
-    const Pointwise<T> pw(a);
-    const int p = nf - 1;
-    for (int idx = threadIdx.x; idx < Reff * L; idx += blockDim.x) {
-      const int r = idx / L, i0 = idx % L;
-      const C c = slot(0, r)[i0];
-      C h = mk<C>(T(0), T(0)), S2 = mk<C>(T(0), T(0));
-      bad |= !(finite_val(c.x) && finite_val(c.y));
-      for (int i = 0; i < p; ++i) {
-        const C e = slot(1 + i, r)[i0];
-        h.x += pw.hpoly(e.x);
-        h.y += pw.hpoly(e.y);
-        S2.x += e.x * e.x;
-        S2.y += e.y * e.y;
-        bad |= !(finite_val(e.x) && finite_val(e.y));
-      }
-      slot(nf, r)[i0] = mk<C>(pw.fc(c.x, h.x), pw.fc(c.y, h.y));
-      for (int i = 0; i < p; ++i) {
-        const C e = slot(1 + i, r)[i0];
-        slot(1 + i, r)[i0] =
-            mk<C>(e.x - pw.Ldt * pw.feta(c.x, e.x, S2.x), e.y - pw.Ldt * pw.feta(c.y, e.y, S2.y));
-      }
-    }
-  }
-  __syncthreads();
-  if (a.mode == 3 && w == nf) return true;  // the diagnostic transforms nf slots
-
-  // phase 3: forward x transform of slot w (c, g_1..g_p, df/dc), packed half
-  // spectra scaled by 2, straight to global memory
-  {
-    C* s = slot(w, g);
-    auto st = [s](int i, C v) { s[pad32(i)] = v; };
-    auto ld = [s](int i) { return s[pad32(i)]; };
-    C v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = s[t + TPL * m];
-    line_fft<L, E, -1>(v, t, twr, st, ld, wsync);
-    wsync();
-#pragma unroll
-    for (int m = 0; m < E; ++m) s[t + TPL * m] = v[m];
-    wsync();
-    C* P = spec + w * a.slot_stride + row * L;
-    if (active) {
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        const int k = t + TPL * m;
-        const C zk = s[k];
-        C out;
-        if (k == 0) {
-          out = mk<C>(T(2) * (zk.x + zk.y), T(2) * (zk.x - zk.y));
+            for (int m = 0; m < E; ++m) dst[t + TPL * m] = cconj(v[m]);
+          }
         } else {
-          const C zm = cconj(s[L - k]);
-          const C A = cadd(zk, zm), B = csub(zk, zm);
-          out = cadd(A, mul_i<-1>(cmul(B, __ldg(&twh[k]))));
+          wsync();
+#pragma unroll
+          for (int m = 0; m < E; ++m) s[t + TPL * m] = cconj(v[m]);
         }
-        P[k] = out;
+      } else {
+        // packed half spectrum, scaled by 2, straight to global memory
+        wsync();
+#pragma unroll
+        for (int m = 0; m < E; ++m) s[t + TPL * m] = v[m];
+        wsync();
+        C* P = spec + w * a.slot_stride + row * L;
+        if (active) {
+#pragma unroll
+          for (int m = 0; m < E; ++m) {
+            const int k = t + TPL * m;
+            const C zk = s[k];
+            C out;
+            if (k == 0) {
+              out = mk<C>(T(2) * (zk.x + zk.y), T(2) * (zk.x - zk.y));
+            } else {
+              const C zm = cconj(s[L - k]);
+              const C A = cadd(zk, zm), B = csub(zk, zm);
+              out = cadd(A, mul_i<-1>(cmul(B, __ldg(&twh[k]))));
+            }
+            P[k] = out;
+          }
+        }
       }
     }
+    if (!inv) break;
+    if (a.mode == 2) return true;
+    __syncthreads();
+
+    // phase 2: pointwise derivative stage, all threads over all R * L pairs
+    if (a.mode == 3) {
+      // chemical free energy f_chem = rho2 (c-ca)^2 (1-h) + rho2 (cb-c)^2 h + w g
+      const Coef<T>& k = coef<T>(a);
+      const T rho2 = k.two_rho2 * T(0.5), cb = k.ca + k.dcab, alpha = k.four_alpha * T(0.25);
+      const Pointwise<T> pw(a);
+      const int p = nf - 1;
+      double sum = 0.0;
+      for (int idx = threadIdx.x; idx < Reff * L; idx += blockDim.x) {
+        const int r = idx / L, i0 = idx % L;
+        const C c = slot(0, r)[i0];
+        T part[2];
+        const T cc[2] = {c.x, c.y};
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          T h = T(0), g = T(0), s2 = T(0), s4 = T(0);
+          for (int i = 0; i < p; ++i) {
+            const C e2 = slot(1 + i, r)[i0];
+            const T e = h2 ? e2.y : e2.x;
+            h += pw.hpoly(e);
+            g += e * e * (T(1) - e) * (T(1) - e);
+            s2 += e * e;
+            s4 += e * e * e * e;
+          }
+          g += alpha * (s2 * s2 - s4);
+          const T da = cc[h2] - k.ca, db = cb - cc[h2];
+          part[h2] = rho2 * da * da * (T(1) - h) + rho2 * db * db * h + k.w * g;
+        }
+        sum += (double)part[0] + (double)part[1];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+      if (lane == 0) atomicAdd(&a.acc[0], sum);
+    } else {
+      const Pointwise<T> pw(a);
+      const int p = nf - 1;
+      for (int idx = threadIdx.x; idx < Reff * L; idx += blockDim.x) {
+        const int r = idx / L, i0 = idx % L;
+        const C c = slot(0, r)[i0];
+        C h = mk<C>(T(0), T(0)), S2 = mk<C>(T(0), T(0));
+        bad |= !(finite_val(c.x) && finite_val(c.y));
+        for (int i = 0; i < p; ++i) {
+          const C e = slot(1 + i, r)[i0];
+          h.x += pw.hpoly(e.x);
+          h.y += pw.hpoly(e.y);
+          S2.x += e.x * e.x;
+          S2.y += e.y * e.y;
+          bad |= !(finite_val(e.x) && finite_val(e.y));
+        }
+        slot(nf, r)[i0] = mk<C>(pw.fc(c.x, h.x), pw.fc(c.y, h.y));
+        for (int i = 0; i < p; ++i) {
+          const C e = slot(1 + i, r)[i0];
+          slot(1 + i, r)[i0] =
+              mk<C>(e.x - pw.Ldt * pw.feta(c.x, e.x, S2.x), e.y - pw.Ldt * pw.feta(c.y, e.y, S2.y));
+        }
+      }
+    }
+    __syncthreads();
   }
   if (bad) atomicOr(a.flag, FS_FLAG_NONFINITE);
   return true;
@@ -405,72 +414,76 @@ __device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap
   C* xt = tiles + (nin - 1) * TROWS * tk;  // exchange tile of the updated field
   auto sync = []() { __syncthreads(); };
 
-  // forward transforms: c group takes df/dc (tile 0) then c (tile 1)
+  // All transforms share one call site (small instruction footprint):
+  // iterations 0..nin-1 are the forward transforms of the loaded tiles (the
+  // c group takes df/dc, kept in tile 0, then c), the last iteration is the
+  // inverse transform, computed as conj(FFT(conj(v))).
   C v[E];
-  for (int i = 0; i < nin; ++i) {
-    C* tl = tiles + i * TROWS * tk + j;
+  for (int it = 0; it <= nin; ++it) {
+    const bool inv = (it == nin);
+    C* tl = (inv ? xt : tiles + it * TROWS * tk) + j;
     auto st = [tl, tk](int q, C x) { tl[(q + (q >> LOGE)) * tk] = x; };
     auto ld = [tl, tk](int q) { return tl[(q + (q >> LOGE)) * tk]; };
+    if (!inv) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = tl[(t + TPL * m) * tk];
+      for (int m = 0; m < E; ++m) v[m] = tl[(t + TPL * m) * tk];
+    } else {
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = cconj(v[m]);
+    }
     line_fft<NY, E, -1>(v, t, twc, st, ld, sync);
-    if (i == 0 && nin == 2) {
+    if (inv) break;
+    if (it + 1 < nin) {
       sync();
 #pragma unroll
       for (int m = 0; m < E; ++m) tl[(t + TPL * m) * tk] = v[m];
+      continue;
     }
-  }
-
-  if (special) {
-    // Separate the packed column Z = A + i B (A: kx = 0, B: kx = nx/2, both
-    // Hermitian in ky) through shared memory, update both, repack.
-    sync();
-    if (j == 0) {
+    // k-space update of the last forward transform
+    if (special) {
+      // Separate the packed column Z = A + i B (A: kx = 0, B: kx = nx/2, both
+      // Hermitian in ky) through shared memory, update both, repack.
+      sync();
+      if (j == 0) {
 #pragma unroll
-      for (int m = 0; m < E; ++m) xt[(t + TPL * m) * tk] = v[m];
-    }
-    sync();
-  }
-  if (special && j == 0) {
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int ky = t + TPL * m, kq = (NY - ky) & (NY - 1);
-      const T ky2 = k2yt[ky];
-      const C pz = cconj(xt[kq * tk]);
-      const C A = cscale(cadd(v[m], pz), T(0.5)), B = cscale(mul_i<-1>(csub(v[m], pz)), T(0.5));
-      C An, Bn;
-      if (g == 0) {
-        const C zf = stash[ky * tk], pf = cconj(stash[kq * tk]);
-        const C Af = cscale(cadd(zf, pf), T(0.5)), Bf = cscale(mul_i<-1>(csub(zf, pf)), T(0.5));
-        An = up.c(A, Af, kx2 + ky2);
-        Bn = up.c(B, Bf, kxn2 + ky2);
-        if (ky == 0 && a.csum) An = mk<C>((T)(*a.csum * a.inv_npts), T(0));
-      } else {
-        An = up.eta(A, kx2 + ky2);
-        Bn = up.eta(B, kxn2 + ky2);
+        for (int m = 0; m < E; ++m) xt[(t + TPL * m) * tk] = v[m];
       }
-      v[m] = cadd(An, mul_i<1>(Bn));
+      sync();
     }
-  } else if (g == 0) {
+    if (special && j == 0) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int ky = t + TPL * m;
-      v[m] = up.c(v[m], stash[ky * tk + j], kx2 + k2yt[ky]);
+      for (int m = 0; m < E; ++m) {
+        const int ky = t + TPL * m, kq = (NY - ky) & (NY - 1);
+        const T ky2 = k2yt[ky];
+        const C pz = cconj(xt[kq * tk]);
+        const C A = cscale(cadd(v[m], pz), T(0.5)), B = cscale(mul_i<-1>(csub(v[m], pz)), T(0.5));
+        C An, Bn;
+        if (g == 0) {
+          const C zf = stash[ky * tk], pf = cconj(stash[kq * tk]);
+          const C Af = cscale(cadd(zf, pf), T(0.5)), Bf = cscale(mul_i<-1>(csub(zf, pf)), T(0.5));
+          An = up.c(A, Af, kx2 + ky2);
+          Bn = up.c(B, Bf, kxn2 + ky2);
+          if (ky == 0 && a.csum) An = mk<C>((T)(*a.csum * a.inv_npts), T(0));
+        } else {
+          An = up.eta(A, kx2 + ky2);
+          Bn = up.eta(B, kxn2 + ky2);
+        }
+        v[m] = cadd(An, mul_i<1>(Bn));
+      }
+    } else if (g == 0) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int ky = t + TPL * m;
+        v[m] = up.c(v[m], stash[ky * tk + j], kx2 + k2yt[ky]);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = up.eta(v[m], kx2 + k2yt[t + TPL * m]);
     }
-  } else {
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = up.eta(v[m], kx2 + k2yt[t + TPL * m]);
-  }
-
-  {
-    C* tl = xt + j;
-    auto st = [tl, tk](int q, C x) { tl[(q + (q >> LOGE)) * tk] = x; };
-    auto ld = [tl, tk](int q) { return tl[(q + (q >> LOGE)) * tk]; };
-    line_fft<NY, E, 1>(v, t, twc, st, ld, sync);
   }
   C* S = reinterpret_cast<C*>(a.spec) + kx + (long long)(g == 0 ? 0 : g) * a.slot_stride;
 #pragma unroll
-  for (int m = 0; m < E; ++m) S[(long long)(t + TPL * m) * Lh] = v[m];
+  for (int m = 0; m < E; ++m) S[(long long)(t + TPL * m) * Lh] = cconj(v[m]);
   return true;
 }
 
@@ -483,7 +496,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
     fs_energy_col_kernel(KArgs a, const __grid_constant__ CUtensorMap tmap) {
   using C = cplx<T>;
   using Cfg = ColCfg<T, NY>;
-  constexpr int E = Cfg::E, TPL = Cfg::TPL, BH = Cfg::BH, TROWS = Cfg::TROWS, LOGE = Cfg::LOGE;
+  constexpr int E = Cfg::E, TPL = Cfg::TPL, BH = Cfg::BH, LOGE = Cfg::LOGE;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   C* twc = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);
