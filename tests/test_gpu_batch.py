@@ -73,7 +73,10 @@ def test_fp32_batch_matches_oracle_per_member(F, O):
 
 def test_batch_equals_single_plans(F):
     """The ensemble launch runs the same per-simulation code as a plan of one:
-    after 40 steps every member agrees with its own single-plan run."""
+    after 40 steps every member agrees with its own single-plan run.  The two
+    kernels are compiled separately (FMA contraction may differ), so FP32
+    rounding differences of one ulp per step grow along the trajectory; a
+    member or parameter mix-up would differ by O(1e-2)."""
     import torch
     probs = I.batch_problems(12, seed=3, sizes=(128, 256, 512))
     fields = [I.noise_fields(pr, seed=40 + i).astype(np.float32) for i, pr in enumerate(probs)]
@@ -84,7 +87,7 @@ def test_batch_equals_single_plans(F):
         plan.step(40)
         ref = plan.get_fields().double().cpu().numpy()
         plan.close()
-        assert rel_linf(g, ref) <= 1e-6
+        assert rel_linf(g, ref) <= 1e-5
 
 
 def test_batch_rejects_unsupported_members(F):
