@@ -44,6 +44,7 @@ struct KArgs {
   int nx, ny, nz, nf;
   long long lines;         // rows handled by a row pass (ny * nz)
   int mode;                // row pass: 0 step from spectra, 1 step from real, 2 inverse only
+  int tc;                  // FP32 column transforms: 0 CUDA cores, 1 TF32 x 3, 2 BF16 x 3 tensor-core stage
   double M, L, kappa_c, kappa_eta, rho2, c_alpha, c_beta, w, alpha, dt;
   double scale;            // k-space scale 1 / (2 N)
   double inv_npts;         // 1 / N

@@ -37,17 +37,27 @@ int col_tk_n(int nx) {
   return Cfg::TK < Lh ? Cfg::TK : Lh;
 }
 
-template <typename T, int NY>
-cudaError_t col_launch_n(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+template <typename T, int NY, int TCM>
+cudaError_t col_launch_tc(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
   using Cfg = ColCfg<T, NY>;
   const int tk = col_tk_n<T, NY>(a.nx);
-  size_t smem = Cfg::HEAD + 2 * (size_t)Cfg::TROWS * tk * sizeof(cplx<T>);
+  size_t smem = col_smem_bytes<T, NY, TCM>(tk);
   static unsigned done = 0;
-  cudaError_t e = allow_big_smem(fs_col_kernel<T, NY>, &done);
+  cudaError_t e = allow_big_smem(fs_col_kernel<T, NY, TCM>, &done);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(a.nx / 2 / tk), (unsigned)a.nf);
-  fs_col_kernel<T, NY><<<grid, (unsigned)(tk * Cfg::TPL), smem, s>>>(a, tm);
+  fs_col_kernel<T, NY, TCM><<<grid, (unsigned)(tk * Cfg::TPL), smem, s>>>(a, tm);
   return cudaGetLastError();
+}
+
+template <typename T, int NY>
+cudaError_t col_launch_n(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4 && NY >= 64) {
+    if (a.tc == TC_TF32) return col_launch_tc<T, NY, TC_TF32>(a, tm, s);
+    if (a.tc == TC_BF16X3) return col_launch_tc<T, NY, TC_BF16X3>(a, tm, s);
+  }
+  if (a.tc != TC_NONE) return cudaErrorInvalidValue;
+  return col_launch_tc<T, NY, TC_NONE>(a, tm, s);
 }
 
 template <typename T, int NY>

@@ -41,7 +41,7 @@ struct LineCfg {
 // y pass: one CTA per (kx tile, z, slot); DIR = -1 forward (slots 0..nf),
 // DIR = +1 inverse (slots 0..nf-1).  Tensor map: [slot * nz + z][y][kx].
 // ---------------------------------------------------------------------------
-template <typename T, int NY, int DIR>
+template <typename T, int NY, int DIR, int TCM = TC_NONE>
 __global__ void __launch_bounds__(LineCfg<T, NY>::THREADS, 2)
     fs_ypass_kernel(KArgs a, const __grid_constant__ CUtensorMap tmap) {
   using C = cplx<T>;
@@ -112,7 +112,20 @@ __global__ void __launch_bounds__(LineCfg<T, NY>::THREADS, 2)
     C* tl = tile + j;
     auto st = [tl, tk](int q, C x) { tl[(q + (q >> LOGE)) * tk] = x; };
     auto ld = [tl, tk](int q) { return tl[(q + (q >> LOGE)) * tk]; };
-    line_fft<NY, E, DIR>(v, t, tw, st, ld, []() { __syncthreads(); });
+    auto sync = []() { __syncthreads(); };
+    if constexpr (TCM != TC_NONE && DIR < 0) {
+      // first radix-16 pass on tensor cores (input still in the tile), rest on CUDA cores
+      static_assert(sizeof(T) == 4 && E == 16, "tensor-core stage: FP32, radix 16");
+      float* bsm = reinterpret_cast<float*>(tile + Cfg::TROWS * tk);
+      tc_fill_b<TCM>(bsm);
+      __syncthreads();
+      tc_first_pass16<NY, TCM>(reinterpret_cast<float2*>(tile), tk, bsm);
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = ld(t + TPL * m);
+      stockham<NY, E, 16, DIR>(v, t, tw, st, ld, sync);
+    } else {
+      line_fft<NY, E, DIR>(v, t, tw, st, ld, sync);
+    }
   }
   if (DIR < 0 && special) {
     // pack: A = (Z(ky) + conj Z(-ky)) / 2, B = (Z(ky) - conj Z(-ky)) / (2i)
@@ -151,7 +164,7 @@ __global__ void __launch_bounds__(LineCfg<T, NY>::THREADS, 2)
 // z step: one CTA per (kx tile, ky storage row, field group).  Tensor map:
 // [slot][z][y][kx] with a box of one y row and up to 256 z planes.
 // ---------------------------------------------------------------------------
-template <typename T, int NZ>
+template <typename T, int NZ, int TCM = TC_NONE>
 __global__ void __launch_bounds__(LineCfg<T, NZ>::THREADS, 2)
     fs_zstep_kernel(KArgs a, const __grid_constant__ CUtensorMap tmap) {
   using C = cplx<T>;
@@ -210,14 +223,27 @@ __global__ void __launch_bounds__(LineCfg<T, NZ>::THREADS, 2)
   C* stash = tiles;
   C* xt = tiles + (nin - 1) * TROWS * tk;
   auto sync = []() { __syncthreads(); };
+  float* bsm = reinterpret_cast<float*>(tiles + 2 * TROWS * tk);
+  if constexpr (TCM != TC_NONE) {
+    static_assert(sizeof(T) == 4 && E == 16, "tensor-core stage: FP32, radix 16");
+    tc_fill_b<TCM>(bsm);
+    __syncthreads();
+  }
   C v[E];
   for (int i = 0; i < nin; ++i) {
     C* tl = tiles + i * TROWS * tk + j;
     auto st = [tl, tk](int q, C x) { tl[(q + (q >> LOGE)) * tk] = x; };
     auto ld = [tl, tk](int q) { return tl[(q + (q >> LOGE)) * tk]; };
+    if constexpr (TCM != TC_NONE) {
+      tc_first_pass16<NZ, TCM>(reinterpret_cast<float2*>(tiles + i * TROWS * tk), tk, bsm);
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = tl[(t + TPL * m) * tk];
-    line_fft<NZ, E, -1>(v, t, tw, st, ld, sync);
+      for (int m = 0; m < E; ++m) v[m] = ld(t + TPL * m);
+      stockham<NZ, E, 16, -1>(v, t, tw, st, ld, sync);
+    } else {
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = tl[(t + TPL * m) * tk];
+      line_fft<NZ, E, -1>(v, t, tw, st, ld, sync);
+    }
     if (i == 0 && nin == 2) {
       sync();
 #pragma unroll
@@ -281,30 +307,50 @@ int line_tk(int nx) {
   return LineCfg<T, NL>::TK < Lh ? LineCfg<T, NL>::TK : Lh;
 }
 
-template <typename T, int NY, int DIR>
-cudaError_t ypass_launch_n(const KArgs& a, const CUtensorMap& tm, int nslots, cudaStream_t s) {
+template <typename T, int NY, int DIR, int TCM>
+cudaError_t ypass_launch_tc(const KArgs& a, const CUtensorMap& tm, int nslots, cudaStream_t s) {
   using Cfg = LineCfg<T, NY>;
   const int tk = line_tk<T, NY>(a.nx);
-  size_t smem = Cfg::HEAD + (size_t)Cfg::TROWS * tk * sizeof(cplx<T>);
+  size_t smem = Cfg::HEAD + (size_t)Cfg::TROWS * tk * sizeof(cplx<T>) + (TCM ? 8192 : 0);
   static unsigned done = 0;
-  cudaError_t e = allow_big_smem(fs_ypass_kernel<T, NY, DIR>, &done);
+  cudaError_t e = allow_big_smem(fs_ypass_kernel<T, NY, DIR, TCM>, &done);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(a.nx / 2 / tk), (unsigned)(a.nz * nslots));
-  fs_ypass_kernel<T, NY, DIR><<<grid, (unsigned)(tk * Cfg::TPL), smem, s>>>(a, tm);
+  fs_ypass_kernel<T, NY, DIR, TCM><<<grid, (unsigned)(tk * Cfg::TPL), smem, s>>>(a, tm);
+  return cudaGetLastError();
+}
+
+template <typename T, int NY, int DIR>
+cudaError_t ypass_launch_n(const KArgs& a, const CUtensorMap& tm, int nslots, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4 && NY >= 64 && DIR < 0) {
+    if (a.tc == TC_TF32) return ypass_launch_tc<T, NY, DIR, TC_TF32>(a, tm, nslots, s);
+    if (a.tc == TC_BF16X3) return ypass_launch_tc<T, NY, DIR, TC_BF16X3>(a, tm, nslots, s);
+  }
+  if (a.tc != TC_NONE && DIR < 0) return cudaErrorInvalidValue;
+  return ypass_launch_tc<T, NY, DIR, TC_NONE>(a, tm, nslots, s);
+}
+
+template <typename T, int NZ, int TCM>
+cudaError_t zstep_launch_tc(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+  using Cfg = LineCfg<T, NZ>;
+  const int tk = line_tk<T, NZ>(a.nx);
+  size_t smem = Cfg::HEAD + 2 * (size_t)Cfg::TROWS * tk * sizeof(cplx<T>) + (TCM ? 8192 : 0);
+  static unsigned done = 0;
+  cudaError_t e = allow_big_smem(fs_zstep_kernel<T, NZ, TCM>, &done);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)(a.nx / 2 / tk), (unsigned)a.ny, (unsigned)a.nf);
+  fs_zstep_kernel<T, NZ, TCM><<<grid, (unsigned)(tk * Cfg::TPL), smem, s>>>(a, tm);
   return cudaGetLastError();
 }
 
 template <typename T, int NZ>
 cudaError_t zstep_launch_n(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
-  using Cfg = LineCfg<T, NZ>;
-  const int tk = line_tk<T, NZ>(a.nx);
-  size_t smem = Cfg::HEAD + 2 * (size_t)Cfg::TROWS * tk * sizeof(cplx<T>);
-  static unsigned done = 0;
-  cudaError_t e = allow_big_smem(fs_zstep_kernel<T, NZ>, &done);
-  if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)(a.nx / 2 / tk), (unsigned)a.ny, (unsigned)a.nf);
-  fs_zstep_kernel<T, NZ><<<grid, (unsigned)(tk * Cfg::TPL), smem, s>>>(a, tm);
-  return cudaGetLastError();
+  if constexpr (sizeof(T) == 4 && NZ >= 64) {
+    if (a.tc == TC_TF32) return zstep_launch_tc<T, NZ, TC_TF32>(a, tm, s);
+    if (a.tc == TC_BF16X3) return zstep_launch_tc<T, NZ, TC_BF16X3>(a, tm, s);
+  }
+  if (a.tc != TC_NONE) return cudaErrorInvalidValue;
+  return zstep_launch_tc<T, NZ, TC_NONE>(a, tm, s);
 }
 
 #define FS_LINE_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512)

@@ -30,6 +30,7 @@
 
 #include "fs_fft.cuh"
 #include "fs_internal.h"
+#include "fs_tc.cuh"
 
 namespace fs {
 
@@ -362,15 +363,17 @@ struct KUpdate {
   }
 };
 
-// Shared memory of one column-pass CTA (bytes) for a tile of tk columns.
-template <typename T, int NY>
+// Shared memory of one column-pass CTA (bytes) for a tile of tk columns
+// (plus the split DFT matrix of the tensor-core stage).
+template <typename T, int NY, int TCM = TC_NONE>
 constexpr size_t col_smem_bytes(int tk) {
-  return ColCfg<T, NY>::HEAD + 2 * (size_t)ColCfg<T, NY>::TROWS * tk * sizeof(cplx<T>);
+  return ColCfg<T, NY>::HEAD + 2 * (size_t)ColCfg<T, NY>::TROWS * tk * sizeof(cplx<T>) + (TCM ? 8192 : 0);
 }
 
 // One column-pass work item: kx tile bx, field group g of the simulation
-// described by `a`, tiles loaded through the tensor map `tmap`.
-template <typename T, int NY>
+// described by `a`, tiles loaded through the tensor map `tmap`.  TCM != 0:
+// the first radix-16 pass of each forward transform runs on tensor cores.
+template <typename T, int NY, int TCM = TC_NONE>
 __device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap, int bx, int g,
                                          unsigned char* smem_raw, uint64_t* bar, uint32_t parity) {
   using C = cplx<T>;
@@ -413,6 +416,12 @@ __device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap
   C* stash = tiles;  // c group: transformed df/dc, natural layout [ky][j]
   C* xt = tiles + (nin - 1) * TROWS * tk;  // exchange tile of the updated field
   auto sync = []() { __syncthreads(); };
+  float* bsm = reinterpret_cast<float*>(tiles + 2 * TROWS * tk);
+  if constexpr (TCM != TC_NONE) {
+    static_assert(sizeof(T) == 4 && E == 16, "tensor-core stage: FP32, radix 16");
+    tc_fill_b<TCM>(bsm);
+    __syncthreads();
+  }
 
   // All transforms share one call site (small instruction footprint):
   // iterations 0..nin-1 are the forward transforms of the loaded tiles (the
@@ -424,14 +433,28 @@ __device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap
     C* tl = (inv ? xt : tiles + it * TROWS * tk) + j;
     auto st = [tl, tk](int q, C x) { tl[(q + (q >> LOGE)) * tk] = x; };
     auto ld = [tl, tk](int q) { return tl[(q + (q >> LOGE)) * tk]; };
-    if (!inv) {
+    if constexpr (TCM != TC_NONE) {
+      if (!inv) {
+        // first radix-16 pass on tensor cores, the rest on CUDA cores
+        tc_first_pass16<NY, TCM>(reinterpret_cast<float2*>(tiles + it * TROWS * tk), tk, bsm);
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = tl[(t + TPL * m) * tk];
+        for (int m = 0; m < E; ++m) v[m] = ld(t + TPL * m);
+        stockham<NY, E, 16, -1>(v, t, twc, st, ld, sync);
+      } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = cconj(v[m]);
+        line_fft<NY, E, -1>(v, t, twc, st, ld, sync);
+      }
     } else {
+      if (!inv) {
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = cconj(v[m]);
+        for (int m = 0; m < E; ++m) v[m] = tl[(t + TPL * m) * tk];
+      } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = cconj(v[m]);
+      }
+      line_fft<NY, E, -1>(v, t, twc, st, ld, sync);
     }
-    line_fft<NY, E, -1>(v, t, twc, st, ld, sync);
     if (inv) break;
     if (it + 1 < nin) {
       sync();
@@ -563,7 +586,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
   if ((threadIdx.x & 31) == 0) atomicAdd(&a.acc[1 + g], sum);
 }
 
-template <typename T, int NY>
+template <typename T, int NY, int TCM = TC_NONE>
 __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
     fs_col_kernel(KArgs a, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -573,7 +596,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
     fence_mbar_init();
   }
   __syncthreads();
-  col_body<T, NY>(a, &tmap, blockIdx.x, blockIdx.y, smem_raw, bar, 0);
+  col_body<T, NY, TCM>(a, &tmap, blockIdx.x, blockIdx.y, smem_raw, bar, 0);
 }
 
 }  // namespace fs

@@ -160,8 +160,11 @@ fs_status validate(const fs_params* p, std::string* why) {
     return FS_ERR_UNSUPPORTED;
   }
   if (p->precision == FS_F32_TC_TF32 || p->precision == FS_F32_TC_BF16X3) {
-    *why = "tensor-core DFT stage is not built in this library version";
-    return FS_ERR_UNSUPPORTED;
+    if (p->scheme != FS_SCHEME_SEMI_IMPLICIT_FS || p->n[0] < 64 || p->n[1] < 64 ||
+        (p->ndim > 2 && p->n[2] < 64)) {
+      *why = "the tensor-core DFT stage needs the FS scheme and every axis of at least 64 points";
+      return FS_ERR_UNSUPPORTED;
+    }
   }
   return FS_OK;
 }
@@ -249,6 +252,7 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   a.nf = p->nf;
   a.lines = (long long)a.ny * a.nz;
   a.mode = mode;
+  a.tc = m.prm.precision == FS_F32_TC_TF32 ? 1 : (m.prm.precision == FS_F32_TC_BF16X3 ? 2 : 0);
   a.M = m.prm.M;
   a.L = m.prm.L;
   a.kappa_c = m.prm.kappa_c;
@@ -575,6 +579,8 @@ fs_status setup_batch(fs_plan* p) {
     const int tk = p->f64 ? fs::col_batch_tk_f64(nx, ny) : fs::col_batch_tk_f32(nx, ny);
     if (nx < 16 || tk == 0)
       return fail(nullptr, FS_ERR_UNSUPPORTED, "batched members need nx >= 16 and ny >= 128 (FP32) / 64 (FP64)");
+    if (m.prm.precision == FS_F32_TC_TF32 || m.prm.precision == FS_F32_TC_BF16X3)
+      return fail(nullptr, FS_ERR_UNSUPPORTED, "batched plans use the CUDA-core transforms (FS_F64 or FS_F32)");
   }
   std::vector<int> order(nm);
   for (int i = 0; i < nm; ++i) order[i] = i;
