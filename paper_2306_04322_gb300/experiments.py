@@ -1,0 +1,106 @@
+"""Configuration-level studies on the GPU (each prints one JSON object).
+
+    python -m paper_2306_04322_gb300.experiments precision   [--steps 2000]
+    python -m paper_2306_04322_gb300.experiments accuracy    [--steps 10000]
+
+precision: 3D 256^3, p = 2, dt = 5e-3 from seeded noise; FP32, TF32 x 3 and
+    BF16 x 3 runs against an FP64 GPU run of the same steps: relative L-inf of
+    every field and the phase fraction (share of points with eta_i > 1/2).
+accuracy: 2D 1024^2, p = 2 (FP64): the semi-implicit FS step at dt = 6 dt_FD
+    and the explicit FD scheme (Section 2.2) at 0.95 dt_FD, both to the same
+    end time, against an FS reference at dt / 16; E_phi of Eq. (error_field)
+    for c and for eta = sum_i eta_i, and the device time each run took.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def _run(fs, pr, f0, steps, precision, scheme=None):
+    import torch
+    dtype = torch.float64 if precision == "f64" else torch.float32
+    plan = fs.Plan(pr, precision, scheme=fs.FS_SCHEME_SEMI_IMPLICIT_FS if scheme is None else scheme)
+    plan.set_fields(torch.as_tensor(f0, dtype=dtype, device="cuda"))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.step(steps)
+    e1.record()
+    out = plan.get_fields().double()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    plan.close()
+    return out, ms
+
+
+def precision_study(steps: int):
+    import torch
+    from . import fs, inputs as I
+    pr = I.Problem(n=(256, 256, 256), p=2)
+    pr.dt = 6.0 * I.fd_stable_dt(pr)
+    f0 = torch.tensor(I.noise_fields(pr, seed=0), dtype=torch.float64, device="cuda")
+    ref, ms_ref = _run(fs, pr, f0, steps, "f64")
+    out = {"workload": "3D 256^3, p=2, dt=5e-3, seeded +-0.01 noise", "steps": steps,
+           "f64": {"ms_per_step": ms_ref / steps,
+                   "phase_fraction": [float((ref[1 + i] > 0.5).double().mean()) for i in range(pr.p)]}}
+    for prec in ("f32", "tf32", "bf16x3"):
+        g, ms = _run(fs, pr, f0.float(), steps, prec)
+        linf = [float((g[f] - ref[f]).abs().max() / ref[f].abs().max()) for f in range(pr.nf)]
+        pf = [float((g[1 + i] > 0.5).double().mean()) for i in range(pr.p)]
+        out[prec] = {"ms_per_step": ms / steps, "rel_linf_vs_f64": linf, "phase_fraction": pf,
+                     "speedup_vs_f64": ms_ref / ms}
+    return out
+
+
+def error_field(ref, phi):
+    """E_phi = int (phi_0 - phi)^2 / int phi_0^2 (Eq. error_field)."""
+    return float(((ref - phi) ** 2).sum() / (ref ** 2).sum())
+
+
+def accuracy_study(steps: int):
+    import torch
+    from . import fs, inputs as I
+    pr = I.Problem(n=(1024, 1024), p=2)
+    dt_fd = I.fd_stable_dt(pr)
+    pr.dt = 6.0 * dt_fd
+    t_end = steps * pr.dt
+    f0 = torch.tensor(I.noise_fields(pr, seed=0), dtype=torch.float64, device="cuda")
+    ref_pr = pr.replace(dt=pr.dt / 16)
+    ref, ms_ref = _run(fs, ref_pr, f0, 16 * steps, "f64")
+    res = {"workload": "2D 1024^2, p=2, seeded +-0.01 noise, FP64", "t_end": t_end,
+           "reference": {"scheme": "FS", "dt": ref_pr.dt, "steps": 16 * steps, "ms": ms_ref}}
+
+    def errs(g):
+        return {"E_c": error_field(ref[0], g[0]), "E_eta": error_field(ref[1:].sum(0), g[1:].sum(0))}
+
+    g, ms = _run(fs, pr, f0, steps, "f64")
+    res["FS_f64"] = {"dt": pr.dt, "steps": steps, "ms": ms, **errs(g)}
+    g, ms = _run(fs, pr, f0.float(), steps, "f32")
+    res["FS_f32"] = {"dt": pr.dt, "steps": steps, "ms": ms, **errs(g)}
+    fd_dt_nominal = 0.95 * dt_fd
+    n_fd = int(np.ceil(t_end / fd_dt_nominal))
+    fd_pr = pr.replace(dt=t_end / n_fd)
+    g, ms = _run(fs, fd_pr, f0, n_fd, "f64", scheme=fs.FS_SCHEME_EXPLICIT_FD)
+    res["FD_f64"] = {"dt": fd_pr.dt, "steps": n_fd, "ms": ms, **errs(g)}
+    res["FD_over_FS_time"] = res["FD_f64"]["ms"] / res["FS_f64"]["ms"]
+    return res
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(prog="python -m paper_2306_04322_gb300.experiments")
+    ap.add_argument("study", choices=["precision", "accuracy"])
+    ap.add_argument("--steps", type=int, default=None)
+    args = ap.parse_args(argv)
+    from . import build as B
+    B.build()
+    if args.study == "precision":
+        out = precision_study(args.steps or 2000)
+    else:
+        out = accuracy_study(args.steps or 10000)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
