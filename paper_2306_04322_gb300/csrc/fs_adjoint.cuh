@@ -50,7 +50,7 @@ __device__ __forceinline__ void hessian_apply(const Pointwise<T>& pw, T c, const
 // u_phi, f_phi(u) into adjoint slots [0, nf), [nf, 2nf), [2nf, 3nf).
 // ---------------------------------------------------------------------------
 template <typename T, int NX>
-__global__ void __launch_bounds__(RowCfg<T, NX>::MAX_THREADS) fs_adj_row_fwd_kernel(KArgs a) {
+__global__ void __launch_bounds__(192) fs_adj_row_fwd_kernel(KArgs a) {
   using C = cplx<T>;
   using Cfg = RowCfg<T, NX>;
   constexpr int L = Cfg::L, E = Cfg::E, TPL = Cfg::TPL, R = Cfg::R, PL = Cfg::PL;
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS) fs_adj_col_kernel(KArg
 // with H at u (a.aux, real); result to a.real (lambda_out).
 // ---------------------------------------------------------------------------
 template <typename T, int NX>
-__global__ void __launch_bounds__(RowCfg<T, NX>::MAX_THREADS) fs_adj_row_inv_kernel(KArgs a) {
+__global__ void __launch_bounds__(192) fs_adj_row_inv_kernel(KArgs a) {
   using C = cplx<T>;
   using Cfg = RowCfg<T, NX>;
   constexpr int L = Cfg::L, E = Cfg::E, TPL = Cfg::TPL, R = Cfg::R, PL = Cfg::PL;

@@ -24,7 +24,7 @@ __device__ __forceinline__ int find_member(const long long* __restrict__ begin, 
 #define FS_BATCH_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 
 template <typename T>
-__global__ void __launch_bounds__(192, RowCfg<T, 1024>::MIN_BLOCKS)
+__global__ void __launch_bounds__(128, RowCfg<T, 1024>::MIN_BLOCKS)
     fs_row_batch_kernel(const KArgs* __restrict__ mem, const long long* __restrict__ begin, int nm,
                         long long total) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -138,7 +138,7 @@ cudaError_t row_batch_launch_t(const BatchArgs& b, cudaStream_t s) {
   static unsigned done = 0;
   cudaError_t e = allow_big_smem(fs_row_batch_kernel<T>, &done);
   if (e != cudaSuccess) return e;
-  fs_row_batch_kernel<T><<<(unsigned)b.row_grid, (unsigned)(32 * b.nf1), b.row_smem, s>>>(
+  fs_row_batch_kernel<T><<<(unsigned)b.row_grid, 128, b.row_smem, s>>>(
       b.mem, b.row_begin, b.nm, b.row_total);
   return cudaGetLastError();
 }

@@ -18,16 +18,35 @@ cudaError_t allow_big_smem(K kernel, unsigned* done_mask) {
   return e;
 }
 
+// Launch with programmatic stream serialisation: the kernel may be scheduled
+// while the previous kernel of the stream is still running.  Only kernels
+// that call griddep_wait() before touching anything the previous kernel
+// writes or reads are launched this way.
+template <typename... KP, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename T, int NX>
 cudaError_t row_launch_n(const KArgs& a, cudaStream_t s) {
   using Cfg = RowCfg<T, NX>;
   const long long reff = a.lines < Cfg::R ? a.lines : Cfg::R;
-  size_t smem = Cfg::BAR_BYTES + Cfg::TW_BYTES + (size_t)(a.nf + 1) * Cfg::R * Cfg::PL * sizeof(cplx<T>);
+  const size_t smem = row_smem_bytes<T, NX>(a.nf);
   static unsigned done = 0;
   cudaError_t e = allow_big_smem(fs_row_kernel<T, NX>, &done);
   if (e != cudaSuccess) return e;
-  fs_row_kernel<T, NX><<<(unsigned)(a.lines / reff), (unsigned)(32 * (a.nf + 1)), smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(fs_row_kernel<T, NX>, dim3((unsigned)(a.lines / reff)), dim3((unsigned)Cfg::THREADS), smem, s, a);
 }
 
 template <typename T, int NY>
@@ -46,8 +65,7 @@ cudaError_t col_launch_tc(const KArgs& a, const CUtensorMap& tm, cudaStream_t s)
   cudaError_t e = allow_big_smem(fs_col_kernel<T, NY, TCM>, &done);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(a.nx / 2 / tk), (unsigned)a.nf);
-  fs_col_kernel<T, NY, TCM><<<grid, (unsigned)(tk * Cfg::TPL), smem, s>>>(a, tm);
-  return cudaGetLastError();
+  return launch_pdl(fs_col_kernel<T, NY, TCM>, grid, dim3((unsigned)(tk * Cfg::TPL)), smem, s, a, tm);
 }
 
 template <typename T, int NY>

@@ -25,7 +25,7 @@ struct LineCfg {
   static constexpr bool F64 = sizeof(T) == 8;
   static constexpr int E = col_E(NL, F64);
   static constexpr int TPL = NL / E;
-  static constexpr int TK = col_tk(NL, F64);
+  static constexpr int TK = col_tk(NL, F64, 128);  // 3D line passes: about 128 threads per CTA
   static constexpr int THREADS = TPL * TK;
   static constexpr int BH = NL < 256 ? NL : 256;  // TMA box extent along the line
   static constexpr int BAR_BYTES = 128;
@@ -42,7 +42,7 @@ struct LineCfg {
 // DIR = +1 inverse (slots 0..nf-1).  Tensor map: [slot * nz + z][y][kx].
 // ---------------------------------------------------------------------------
 template <typename T, int NY, int DIR, int TCM = TC_NONE>
-__global__ void __launch_bounds__(LineCfg<T, NY>::THREADS, 2)
+__global__ void __launch_bounds__(LineCfg<T, NY>::THREADS, 4)
     fs_ypass_kernel(KArgs a, const __grid_constant__ CUtensorMap tmap) {
   using C = cplx<T>;
   using Cfg = LineCfg<T, NY>;
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(LineCfg<T, NY>::THREADS, 2)
 // [slot][z][y][kx] with a box of one y row and up to 256 z planes.
 // ---------------------------------------------------------------------------
 template <typename T, int NZ, int TCM = TC_NONE>
-__global__ void __launch_bounds__(LineCfg<T, NZ>::THREADS, 2)
+__global__ void __launch_bounds__(LineCfg<T, NZ>::THREADS, 4)
     fs_zstep_kernel(KArgs a, const __grid_constant__ CUtensorMap tmap) {
   using C = cplx<T>;
   using Cfg = LineCfg<T, NZ>;

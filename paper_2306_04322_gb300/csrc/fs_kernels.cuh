@@ -75,9 +75,10 @@ __device__ __forceinline__ bool finite_val(T x) {
 }
 
 // ---------------------------------------------------------------------------
-// Row pass.  Lines along x.  A CTA holds R rows and nf + 1 warps; warp w
-// works on field w of all R rows (TPL = L / E threads per line, 32 / TPL lines
-// per warp), so the independent transforms of the fields run in parallel:
+// Row pass.  Lines along x.  A CTA holds R rows and four warps; warp w
+// works on fields w, w + 4, ... of all R rows (TPL = L / E threads per line,
+// 32 / TPL lines per warp), so the independent transforms of the fields run
+// in parallel:
 //   load    one thread issues bulk-async copies of every field's R rows
 //           (packed half spectra, or real pairs in mode 1) into the slots;
 //   phase 1 warp f < nf: inverse x transform of field f (modes 0 and 2);
@@ -102,8 +103,8 @@ struct RowCfg {
   static constexpr int TPL = L / E;
   static constexpr int R = row_R(L, F64);                 // rows per CTA
   static constexpr int PL = (padded_len(L) + 1) & ~1;  // even: 16-byte aligned slots
-  static constexpr int MAX_THREADS = 6 * 32;            // nf + 1 <= 6 warps
-  static constexpr int MIN_BLOCKS = F64 ? 2 : 4;
+  static constexpr int THREADS = 4 * 32;                // four warps; warp w takes fields w, w + 4, ...
+  static constexpr int MIN_BLOCKS = F64 ? 3 : 7;
   static constexpr int BAR_BYTES = 128;
   static constexpr int TWS = pass_table_size(L, E);  // twiddle entries (complex)
   static constexpr int TW_BYTES = ((TWS * (int)sizeof(cplx<T>)) + 127) & ~127;
@@ -116,17 +117,37 @@ constexpr size_t row_smem_bytes(int nf) {
          (size_t)(nf + 1) * RowCfg<T, NX>::R * RowCfg<T, NX>::PL * sizeof(cplx<T>);
 }
 
-// One row-pass work item: row block rb of the simulation described by `a`.
-// `bar` is an initialised mbarrier whose next phase has parity `parity`.
-// Returns false if a bounded wait gave up (the caller must stop).
+// Issues the bulk-async copies of row block rb (every field's rows) into
+// the input slots `in` ([nf][R][PL]), completion on `bar`.  One thread only.
 template <typename T, int NX>
-__device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned char* smem_raw, uint64_t* bar,
-                                         uint32_t parity) {
+__device__ __forceinline__ void row_issue(const KArgs& a, long long rb, cplx<T>* in, uint64_t* bar) {
+  using C = cplx<T>;
+  using Cfg = RowCfg<T, NX>;
+  constexpr int L = Cfg::L, R = Cfg::R, PL = Cfg::PL;
+  const int nf = a.nf;
+  const int Reff = a.lines < R ? (int)a.lines : R;
+  const long long row0 = rb * Reff;
+  const uint32_t bytes = (uint32_t)(L * sizeof(C));
+  const bool from_real = (a.mode == 1 || a.mode == 3);
+  const C* realc = reinterpret_cast<const C*>(a.real);
+  const C* spec = reinterpret_cast<const C*>(a.spec);
+  mbar_arrive_expect_tx(bar, bytes * Reff * nf);
+  for (int f = 0; f < nf; ++f) {
+    // the R rows of field f are contiguous in global memory
+    const C* src = from_real ? realc + f * (a.npts / 2) + row0 * L : spec + f * a.slot_stride + row0 * L;
+    for (int r = 0; r < Reff; ++r) bulk_g2s(in + (f * R + r) * PL, src + r * L, bytes, bar);
+  }
+}
+
+// Compute part of one row-pass work item (row block rb) once its rows have
+// landed: input slots `in` ([nf][R][PL], fields in natural layout), scratch
+// slot `scr` ([R][PL], df/dc), pass tables `twr` in shared memory.
+template <typename T, int NX>
+__device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T>* in, cplx<T>* scr,
+                                            const cplx<T>* twr) {
   using C = cplx<T>;
   using Cfg = RowCfg<T, NX>;
   constexpr int L = Cfg::L, E = Cfg::E, TPL = Cfg::TPL, R = Cfg::R, PL = Cfg::PL;
-  C* twr = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);
-  C* slots = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES + Cfg::TW_BYTES);  // [(nf + 1) * R][PL]
   const int nf = a.nf;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / TPL, t = lane % TPL;  // row within the CTA, thread within the line
@@ -139,25 +160,13 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
   C* realc = reinterpret_cast<C*>(a.real);  // real row as complex pairs
   const long long half_stride = a.npts / 2;  // complex pairs per real field
   auto wsync = []() { __syncwarp(); };
-  copy_to_smem(twr, reinterpret_cast<const C*>(a.tw_row), Cfg::TWS);
-  auto slot = [slots](int f, int r) { return slots + (f * R + r) * PL; };
-  __syncthreads();
-
-  // load: the R rows of field f are contiguous in global memory
-  if (threadIdx.x == 0) {
-    const uint32_t bytes = (uint32_t)(L * sizeof(C));
-    mbar_arrive_expect_tx(bar, bytes * Reff * nf);
-    for (int f = 0; f < nf; ++f) {
-      const bool from_real = (a.mode == 1 || a.mode == 3);
-      const C* src = from_real ? realc + f * half_stride + row0 * L : spec + f * a.slot_stride + row0 * L;
-      for (int r = 0; r < Reff; ++r) bulk_g2s(slot(f, r), src + r * L, bytes, bar);
-    }
-  }
-  if (!mbar_wait_bounded(bar, parity, kWaitPolls)) {
-    if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
-    mbar_wait_bounded(bar, parity, kWaitPolls);  // let the copies land before exiting
-    return false;
-  }
+  auto slot = [in, scr, nf](int f, int r) { return f < nf ? in + (f * R + r) * PL : scr + r * PL; };
+  // Twiddles of the real <-> half-length complex step, W_k = exp(-2 pi i k / (2L))
+  // for k = t + TPL m: W_t (one table entry) times the exact constant
+  // exp(-2 pi i m / (2E)), 2E <= 32.
+  static_assert(2 * E <= 32, "half-step twiddle constants need 2E <= 32");
+  const C wt = __ldg(&twh[t]);
+  auto wk = [wt](int m) { return twiddle_small<-1>(wt, m, 2 * E); };
 
   // Both transform phases share one FFT call site (small instruction
   // footprint); the inverse is computed as conj(FFT(conj(.))).
@@ -165,11 +174,15 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
   //   phase 2         : pointwise stage, all threads
   //   phase 3 (ph = 1): warp o <= nf, forward x transform of slot o
   bool bad = false;
+  const int nw = blockDim.x >> 5;
   for (int ph = 0; ph < 2; ++ph) {
     const bool inv = (ph == 0);
-    const bool busy = inv ? ((a.mode == 0 || a.mode == 2) && w < nf) : !(a.mode == 3 && w == nf);
-    if (busy) {
-      C* s = slot(w, g);
+    // transforms of this phase: inverse of the nf fields (modes 0, 2), forward
+    // of c, g_1..g_p, df/dc (nf slots only for the diagnostic, mode 3); warp
+    // w takes items w, w + nw, ...
+    const int items = inv ? ((a.mode == 0 || a.mode == 2) ? nf : 0) : (a.mode == 3 ? nf : nf + 1);
+    for (int f = w; f < items; f += nw) {
+      C* s = slot(f, g);
       auto st = [s](int i, C v) { s[pad32(i)] = v; };
       auto ld = [s](int i) { return s[pad32(i)]; };
       C v[E];
@@ -186,7 +199,7 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
           } else {
             const C pm = cconj(s[L - k]);
             const C A = cadd(pk, pm), B = csub(pk, pm);
-            z = cadd(A, mul_i<1>(mul_tw<1>(B, __ldg(&twh[k]))));
+            z = cadd(A, mul_i<1>(mul_tw<1>(B, wk(m))));
           }
           v[m] = cconj(z);
         }
@@ -197,7 +210,7 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
       line_fft<L, E, -1>(v, t, twr, st, ld, wsync);
       if (inv) {
         if (a.mode == 2) {
-          C* dst = realc + w * half_stride + row * L;
+          C* dst = realc + f * half_stride + row * L;
           if (active) {
 #pragma unroll
             for (int m = 0; m < E; ++m) dst[t + TPL * m] = cconj(v[m]);
@@ -213,7 +226,7 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
 #pragma unroll
         for (int m = 0; m < E; ++m) s[t + TPL * m] = v[m];
         wsync();
-        C* P = spec + w * a.slot_stride + row * L;
+        C* P = spec + f * a.slot_stride + row * L;
         if (active) {
 #pragma unroll
           for (int m = 0; m < E; ++m) {
@@ -225,7 +238,7 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
             } else {
               const C zm = cconj(s[L - k]);
               const C A = cadd(zk, zm), B = csub(zk, zm);
-              out = cadd(A, mul_i<-1>(cmul(B, __ldg(&twh[k]))));
+              out = cadd(A, mul_i<-1>(cmul(B, wk(m))));
             }
             P[k] = out;
           }
@@ -233,7 +246,7 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
       }
     }
     if (!inv) break;
-    if (a.mode == 2) return true;
+    if (a.mode == 2) return;
     __syncthreads();
 
     // phase 2: pointwise derivative stage, all threads over all R * L pairs
@@ -296,11 +309,37 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
     __syncthreads();
   }
   if (bad) atomicOr(a.flag, FS_FLAG_NONFINITE);
+}
+
+// One row-pass work item with its own table copy and load (ensemble kernel):
+// `bar` is an initialised mbarrier whose next phase has parity `parity`.
+// Returns false if a bounded wait gave up (the caller must stop).
+template <typename T, int NX>
+__device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned char* smem_raw, uint64_t* bar,
+                                         uint32_t parity) {
+  using C = cplx<T>;
+  using Cfg = RowCfg<T, NX>;
+  C* twr = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);
+  C* slots = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES + Cfg::TW_BYTES);  // [(nf + 1) * R][PL]
+  copy_to_smem(twr, reinterpret_cast<const C*>(a.tw_row), Cfg::TWS);
+  __syncthreads();
+  // everything above only touched constant tables; the spectra are the
+  // previous pass's output
+  griddep_wait();
+  if (threadIdx.x == 0) row_issue<T, NX>(a, rb, slots, bar);
+  griddep_launch_dependents();
+  if (!mbar_wait_bounded(bar, parity, kWaitPolls)) {
+    if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
+    mbar_wait_bounded(bar, parity, kWaitPolls);  // let the copies land before exiting
+    return false;
+  }
+  row_compute<T, NX>(a, rb, slots, slots + a.nf * Cfg::R * Cfg::PL, twr);
   return true;
 }
 
+
 template <typename T, int NX>
-__global__ void __launch_bounds__(RowCfg<T, NX>::MAX_THREADS, RowCfg<T, NX>::MIN_BLOCKS)
+__global__ void __launch_bounds__(RowCfg<T, NX>::THREADS, RowCfg<T, NX>::MIN_BLOCKS)
     fs_row_kernel(KArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -393,6 +432,7 @@ __device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap
   const T* __restrict__ k2xt = reinterpret_cast<const T*>(a.k2x);
 
   if (threadIdx.x == 0) {
+    griddep_wait();  // the tiles are the previous pass's output
     mbar_arrive_expect_tx(bar, (uint32_t)(nin * NY * tk * sizeof(C)));
     const int cx = kx0 * (int)(sizeof(C) / 8);  // innermost coordinate in 8-byte units
     for (int i = 0; i < nin; ++i) {
@@ -402,6 +442,8 @@ __device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap
   }
   copy_to_smem(twc, reinterpret_cast<const C*>(a.tw_col), Cfg::TWS);
   for (int i = threadIdx.x; i < NY; i += blockDim.x) k2yt[i] = reinterpret_cast<const T*>(a.k2y)[i];
+  griddep_wait();
+  griddep_launch_dependents();
   __syncthreads();
   if (!mbar_wait_bounded(bar, parity, kWaitPolls)) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);

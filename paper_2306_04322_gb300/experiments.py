@@ -3,13 +3,19 @@
     python -m paper_2306_04322_gb300.experiments precision   [--steps 2000]
     python -m paper_2306_04322_gb300.experiments accuracy    [--steps 10000]
 
-precision: 3D 256^3, p = 2, dt = 5e-3 from seeded noise; FP32, TF32 x 3 and
-    BF16 x 3 runs against an FP64 GPU run of the same steps: relative L-inf of
-    every field and the phase fraction (share of points with eta_i > 1/2).
+Both start from the benchmark initial condition of Section 3 (Eqs. ic_c,
+ic_eta with p = 2, dx = 1), made periodic as the paper does: the explicit FD
+scheme, run in FP64 on the GPU at half its stable dt, takes it to t = 1.
+
+precision: 3D 256^3, p = 2, dt = 5e-3: the t = 1 state of the 256^2 problem
+    extruded along z (Eq. ic_eta_3d, c = c0); FP32, TF32 x 3 and BF16 x 3 runs
+    against an FP64 GPU run of the same steps: relative L-inf of every field
+    and the phase fraction (share of points with eta_i > 1/2).
 accuracy: 2D 1024^2, p = 2 (FP64): the semi-implicit FS step at dt = 6 dt_FD
-    and the explicit FD scheme (Section 2.2) at 0.95 dt_FD, both to the same
-    end time, against an FS reference at dt / 16; E_phi of Eq. (error_field)
-    for c and for eta = sum_i eta_i, and the device time each run took.
+    (spectral |xi|^2 and the FS-FD O(dl^2) / O(dl^4) forms) and the explicit
+    FD scheme (Section 2.2) at 0.95 dt_FD, all to the same end time, against
+    a spectral FS reference at dt / 16; E_phi of Eq. (error_field) for c and
+    for eta = sum_i eta_i, and the device time each run took.
 """
 from __future__ import annotations
 
@@ -35,14 +41,31 @@ def _run(fs, pr, f0, steps, precision, scheme=None):
     return out, ms
 
 
+def periodic_benchmark_state(fs, pr2d, t_end: float = 1.0):
+    """Benchmark initial condition (Section 3) advanced to t_end by the
+    explicit FD scheme in FP64 at half its stable dt; an (nf, ny, nx) float64
+    CUDA tensor."""
+    import torch
+    from . import inputs as I
+    n = int(np.ceil(t_end / (0.5 * I.fd_stable_dt(pr2d))))
+    pre = pr2d.replace(dt=t_end / n)
+    f0 = torch.tensor(I.benchmark_ic_fields(pr2d), dtype=torch.float64, device="cuda")
+    out, _ = _run(fs, pre, f0, n, "f64", scheme=fs.FS_SCHEME_EXPLICIT_FD)
+    return out
+
+
 def precision_study(steps: int):
     import torch
     from . import fs, inputs as I
     pr = I.Problem(n=(256, 256, 256), p=2)
     pr.dt = 6.0 * I.fd_stable_dt(pr)
-    f0 = torch.tensor(I.noise_fields(pr, seed=0), dtype=torch.float64, device="cuda")
+    s2d = periodic_benchmark_state(fs, I.Problem(n=(256, 256), p=2)).cpu().numpy()
+    f0 = torch.tensor(I.extrude_3d(s2d, 256), dtype=torch.float64, device="cuda")
+    del s2d
     ref, ms_ref = _run(fs, pr, f0, steps, "f64")
-    out = {"workload": "3D 256^3, p=2, dt=5e-3, seeded +-0.01 noise", "steps": steps,
+    out = {"workload": "3D 256^3, p=2, dt=5e-3, benchmark IC at t=1 extruded along z (Eq. ic_eta_3d)",
+           "steps": steps,
+           "initial_phase_fraction": [float((f0[1 + i] > 0.5).double().mean()) for i in range(pr.p)],
            "f64": {"ms_per_step": ms_ref / steps,
                    "phase_fraction": [float((ref[1 + i] > 0.5).double().mean()) for i in range(pr.p)]}}
     for prec in ("f32", "tf32", "bf16x3"):
@@ -66,10 +89,10 @@ def accuracy_study(steps: int):
     dt_fd = I.fd_stable_dt(pr)
     pr.dt = 6.0 * dt_fd
     t_end = steps * pr.dt
-    f0 = torch.tensor(I.noise_fields(pr, seed=0), dtype=torch.float64, device="cuda")
+    f0 = periodic_benchmark_state(fs, pr)
     ref_pr = pr.replace(dt=pr.dt / 16)
     ref, ms_ref = _run(fs, ref_pr, f0, 16 * steps, "f64")
-    res = {"workload": "2D 1024^2, p=2, seeded +-0.01 noise, FP64", "t_end": t_end,
+    res = {"workload": "2D 1024^2, p=2, benchmark IC at t=1, FP64", "t_start": 1.0, "t_end": 1.0 + t_end,
            "reference": {"scheme": "FS", "dt": ref_pr.dt, "steps": 16 * steps, "ms": ms_ref}}
 
     def errs(g):
@@ -79,6 +102,9 @@ def accuracy_study(steps: int):
     res["FS_f64"] = {"dt": pr.dt, "steps": steps, "ms": ms, **errs(g)}
     g, ms = _run(fs, pr, f0.float(), steps, "f32")
     res["FS_f32"] = {"dt": pr.dt, "steps": steps, "ms": ms, **errs(g)}
+    for name, lap in (("FSFD2_f64", 1), ("FSFD4_f64", 2)):
+        g, ms = _run(fs, pr.replace(lap=lap), f0, steps, "f64")
+        res[name] = {"dt": pr.dt, "steps": steps, "ms": ms, **errs(g)}
     fd_dt_nominal = 0.95 * dt_fd
     n_fd = int(np.ceil(t_end / fd_dt_nominal))
     fd_pr = pr.replace(dt=t_end / n_fd)

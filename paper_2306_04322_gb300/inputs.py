@@ -147,6 +147,56 @@ def tanh_slab_fields(prob: Problem, a: float, b: float, width: float,
     return f
 
 
+def benchmark_ic_fields(prob: Problem, c0: float = 0.5, eps: float = 0.05, eta_nu: float = 0.1,
+                        psi: float = 1.5) -> np.ndarray:
+    """The 2D benchmark initial condition of Section 3 (Eqs. ic_c and ic_eta),
+    sampled at x = j dx, y = k dx, for eta_i with i = 1..p:
+
+      c     = c0 + eps [cos(.105x)cos(.11y) + (cos(.13x)cos(.087y))^2
+                        + cos(.025x - .15y)cos(.07x - .02y)]
+      eta_i = eta_nu {cos(.01i x - 4)cos((.007 + .01i)y)
+                      + cos((.11 + .01i)x)cos((.11 + .01i)y)
+                      + psi [cos((.046 + .001i)x + (.0405 + .001i)y)
+                             cos((.031 + .001i)x - (.004 + .001i)y)]^2}^2
+
+    The fields are not periodic on the grid; Section 3 smooths them with the
+    explicit FD scheme up to t = 1 before use (done by the caller)."""
+    if prob.ndim != 2:
+        raise ValueError("the benchmark initial condition is two-dimensional")
+    x, y = grid_coords(prob)
+    f = np.empty((prob.nf,) + prob.shape)
+    f[0] = c0 + eps * (np.cos(0.105 * x) * np.cos(0.11 * y)
+                       + (np.cos(0.13 * x) * np.cos(0.087 * y)) ** 2
+                       + np.cos(0.025 * x - 0.15 * y) * np.cos(0.07 * x - 0.02 * y))
+    for i in range(1, prob.p + 1):
+        a = np.cos(0.01 * i * x - 4.0) * np.cos((0.007 + 0.01 * i) * y)
+        b = np.cos((0.11 + 0.01 * i) * x) * np.cos((0.11 + 0.01 * i) * y)
+        q = (np.cos((0.046 + 0.001 * i) * x + (0.0405 + 0.001 * i) * y)
+             * np.cos((0.031 + 0.001 * i) * x - (0.004 + 0.001 * i) * y))
+        f[i] = eta_nu * (a + b + psi * q * q) ** 2
+    return f
+
+
+def extrude_3d(fields2d: np.ndarray, nz: int, dz: float = 1.0, c0: float = 0.5,
+               zscale: float = 5.0, power: int = 4, clip: float = 1e-9) -> np.ndarray:
+    """3D fields from a 2D state (Eq. ic_eta_3d): c = c0 everywhere and
+
+      eta_i(x, y, z) = (1 + tanh(artanh(2 eta_i^2D(x, y) - 1) - ((z - lz/2)/zscale)^power)) / 2,
+
+    lz = nz dz.  The 2D field is taken index by index (the paper's (2x, 2y)
+    maps its 200-wide 2D domain onto the 100-wide cube; here both grids have
+    the same number of points per axis).  2 eta - 1 is clipped to
+    [-1 + clip, 1 - clip] so artanh stays finite.  Shape (nf, nz, ny, nx)."""
+    nf, ny, nx = fields2d.shape
+    z = (np.arange(nz) * dz - 0.5 * nz * dz)[:, None, None]
+    out = np.empty((nf, nz, ny, nx))
+    out[0] = c0
+    for i in range(1, nf):
+        a = np.arctanh(np.clip(2.0 * fields2d[i] - 1.0, -1.0 + clip, 1.0 - clip))
+        out[i] = 0.5 * (1.0 + np.tanh(a[None, :, :] - (z / zscale) ** power))
+    return out
+
+
 def batch_problems(count: int, seed: int = 0, sizes=(128, 256, 512, 1024), p: int = 2,
                    spread: float = 0.5, dt_factor: float = 5.0):
     """Ensemble of 2D problems: size uniform from `sizes` (square grids) and
