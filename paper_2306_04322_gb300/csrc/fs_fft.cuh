@@ -72,6 +72,25 @@ template <> __device__ __forceinline__ float2 cscale<float2>(float2 a, float s) 
   return upk2(d);
 }
 
+// Lane-wise arithmetic on two independent reals held in one complex-type
+// pair (the row pass keeps two adjacent grid points per pair).  FP32: packed
+// f32x2 instructions; FP64: two scalar lanes.
+template <typename C> __device__ __forceinline__ C vsplat(decltype(C::x) s) { return mk<C>(s, s); }
+template <typename C> __device__ __forceinline__ C vmul(C a, C b) { return mk<C>(a.x * b.x, a.y * b.y); }
+template <typename C> __device__ __forceinline__ C vfma(C a, C b, C c) {
+  return mk<C>(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <> __device__ __forceinline__ float2 vmul<float2>(float2 a, float2 b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
+template <> __device__ __forceinline__ float2 vfma<float2>(float2 a, float2 b, float2 c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+  return upk2(d);
+}
+
 // multiply by +i (DIR = +1) or -i (DIR = -1)
 template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a) {
   return DIR > 0 ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);

@@ -67,6 +67,27 @@ struct Pointwise {
     T well = T(2) * e * (T(1) - e) * (T(1) - T(2) * e) + four_alpha * e * (S2 - e * e);
     return chem + w * well;
   }
+  // The same on two lanes (two grid points per pair, lane-wise arithmetic).
+  template <typename V>
+  __device__ __forceinline__ V hpoly2(V e) const {  // e^3 (e (6 e - 15) + 10)
+    const V t = vfma(e, vfma(e, vsplat<V>(T(6)), vsplat<V>(T(-15))), vsplat<V>(T(10)));
+    return vmul(vmul(vmul(e, e), e), t);
+  }
+  template <typename V>
+  __device__ __forceinline__ V fc2(V c, V h) const {  // 2 rho2 (c - c_a - (c_b - c_a) h)
+    return vmul(vsplat<V>(two_rho2), vfma(h, vsplat<V>(-dcab), csub(c, vsplat<V>(ca))));
+  }
+  // g = eta - L dt df/deta
+  template <typename V>
+  __device__ __forceinline__ V g2(V c, V e, V S2) const {
+    const V q = vfma(e, mk<V>(-e.x, -e.y), e);                                     // e (1 - e)
+    const V chem = vmul(vmul(vsplat<V>(T(30) * rho2dcab), vmul(q, q)),
+                        vfma(c, vsplat<V>(T(-2)), vsplat<V>(cab)));                // h'(e) rho2 dcab (cab - 2c)
+    const V dw = vmul(q, vfma(e, vsplat<V>(T(-2)), vsplat<V>(T(1))));            // e (1 - e)(1 - 2e)
+    const V pair = vmul(e, vfma(e, mk<V>(-e.x, -e.y), S2));                      // e (S2 - e^2)
+    const V well = vfma(dw, vsplat<V>(T(2)), vmul(vsplat<V>(four_alpha), pair));
+    return vfma(vfma(well, vsplat<V>(w), chem), vsplat<V>(-Ldt), e);
+  }
 };
 
 template <typename T>
@@ -287,22 +308,20 @@ __device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T
       const int p = nf - 1;
       for (int idx = threadIdx.x; idx < Reff * L; idx += blockDim.x) {
         const int r = idx / L, i0 = idx % L;
+        // two grid points per pair, lane-wise
         const C c = slot(0, r)[i0];
-        C h = mk<C>(T(0), T(0)), S2 = mk<C>(T(0), T(0));
+        C h = vsplat<C>(T(0)), S2 = vsplat<C>(T(0));
         bad |= !(finite_val(c.x) && finite_val(c.y));
         for (int i = 0; i < p; ++i) {
           const C e = slot(1 + i, r)[i0];
-          h.x += pw.hpoly(e.x);
-          h.y += pw.hpoly(e.y);
-          S2.x += e.x * e.x;
-          S2.y += e.y * e.y;
+          h = cadd(h, pw.hpoly2(e));
+          S2 = vfma(e, e, S2);
           bad |= !(finite_val(e.x) && finite_val(e.y));
         }
-        slot(nf, r)[i0] = mk<C>(pw.fc(c.x, h.x), pw.fc(c.y, h.y));
+        slot(nf, r)[i0] = pw.fc2(c, h);
         for (int i = 0; i < p; ++i) {
           const C e = slot(1 + i, r)[i0];
-          slot(1 + i, r)[i0] =
-              mk<C>(e.x - pw.Ldt * pw.feta(c.x, e.x, S2.x), e.y - pw.Ldt * pw.feta(c.y, e.y, S2.y));
+          slot(1 + i, r)[i0] = pw.g2(c, e, S2);
         }
       }
     }
@@ -393,7 +412,7 @@ struct KUpdate {
   __device__ __forceinline__ C c(C zc, C zf, T k2) const {
     T d = scale / (T(1) + Mdtkc * k2 * k2);
     T b = Mdt * k2;
-    return mk<C>((zc.x - b * zf.x) * d, (zc.y - b * zf.y) * d);
+    return cscale(vfma(zf, vsplat<C>(-b), zc), d);
   }
   // eta^' = g^ / (1 + L dt kappa_eta K2), times the 1/(2N) scale
   template <typename C>
