@@ -72,9 +72,9 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def dram_traffic(kernel: str, precision: str):
-    """DRAM bytes per launch from the committed ncu summary, or None."""
-    path = os.path.join(ROOT, "profiles", "traffic_2d_1024_p2.txt")
+def dram_traffic(kernel: str, precision: str, table: str = "traffic_2d_1024_p2.txt"):
+    """DRAM bytes per launch from a committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", table)
     try:
         for line in open(path):
             parts = line.split()
@@ -271,13 +271,14 @@ def time_plan(probs, precision: str, steps: int, warmup: int, device: int, flush
             "workspace_bytes": ws, "npts": npts, "schedule": sched}
 
 
-def roofline_entry(names, alg_bytes, r, peak, peak_kind):
+def roofline_entry(names, alg_bytes, r, peak, peak_kind, traffic_table=None):
     avg_ms = [m / max(c, 1) for m, c in zip(r["kern_ms"], r["kern_cnt"])]
     dom = max(range(len(avg_ms)), key=lambda i: r["kern_ms"][i])
     achieved = alg_bytes[dom] / (avg_ms[dom] / 1e3) / 1e9
+    traffic = dram_traffic(names[dom], "f32", traffic_table) if traffic_table else None
     return {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes[dom],
-            "avg_launch_ms": avg_ms[dom],
+            "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
+            "alg_bytes_per_launch": alg_bytes[dom], "avg_launch_ms": avg_ms[dom],
             "kernels": {n: {"avg_ms": a, "launches": c, "share": m / max(sum(r["kern_ms"]), 1e-30),
                             "alg_GBps": b / (a / 1e3) / 1e9 if a > 0 else None}
                         for n, a, c, m, b in zip(names, avg_ms, r["kern_cnt"], r["kern_ms"], alg_bytes)}}
@@ -299,7 +300,7 @@ def extras(steps: int, warmup: int, device: int, peak, peak_kind):
                             "workspace_bytes": r["workspace_bytes"],
                             "roofline": roofline_entry(["x_pass(fs_row_kernel)", "fs_ypass_kernel<-1>",
                                                         "fs_zstep_kernel", "fs_ypass_kernel<+1>"],
-                                                       alg, r, peak, peak_kind)}
+                                                       alg, r, peak, peak_kind, "traffic_3d_256_p2.txt")}
     probs = I.batch_problems(512, seed=0)
     kb = max(3, min(steps, 10))
     r = time_plan(probs, "f32", kb, min(warmup, 3), device)
