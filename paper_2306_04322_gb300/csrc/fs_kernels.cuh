@@ -123,7 +123,12 @@ struct RowCfg {
   static constexpr int E = row_E(L, F64);
   static constexpr int TPL = L / E;
   static constexpr int R = row_R(L, F64);                 // rows per CTA
-  static constexpr int PL = (padded_len(L) + 1) & ~1;  // even: 16-byte aligned slots
+  // Slot pitch (complex): even, so every slot is 16-byte aligned for the bulk
+  // copies.  With R > 1 lines per warp the pitch is also chosen = TPL/2 (mod
+  // TPL): the lines of a half-warp then start on different banks and the
+  // stride-TPL accesses are conflict-free (one line per warp needs nothing).
+  static constexpr int PL0 = (padded_len(L) + 1) & ~1;
+  static constexpr int PL = (R > 1 && TPL >= 4) ? PL0 + ((TPL / 2 - PL0 % TPL) + TPL) % TPL : PL0;
   static constexpr int THREADS = 4 * 32;                // four warps; warp w takes fields w, w + 4, ...
   static constexpr int MIN_BLOCKS = F64 ? 3 : 7;
   static constexpr int BAR_BYTES = 128;
