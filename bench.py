@@ -423,6 +423,25 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def reduce_max(v: float, dist, device: str = "cpu") -> float:
+    """Maximum of a per-rank float over the process group (identity without
+    one); `device` is where the reduction tensor lives (CUDA for NCCL, CPU for
+    gloo)."""
+    if not dist:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, npts: int, steps: int, slowest_seconds: float) -> float:
+    """Whole-job throughput of independent replicas: every rank advanced its
+    own simulation of npts points by `steps` steps; the job took as long as
+    the slowest rank."""
+    return world * npts * steps / slowest_seconds
+
+
 def main():
     args = parse()
     world, rank, local = dist_info()
@@ -446,11 +465,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(v: float) -> float:
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, dist, f"cuda:{local}")
 
     barrier()
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -470,7 +485,7 @@ def main():
     t64 = max_over_ranks(r64["total_ms"]) / 1e3
     te2e = max_over_ranks(e2e["seconds"])
     npts = r32["npts"]
-    value = world * npts * args.steps / t32
+    value = job_value(world, npts, args.steps, t32)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -502,13 +517,13 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "workspace_bytes": r32["workspace_bytes"]},
         "roofline": roof,
-        "e2e": {"value": world * npts * args.steps / te2e, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
+        "e2e": {"value": job_value(world, npts, args.steps, te2e), "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
                 "d2h_bytes_per_step": e2e["d2h"],
                 "how": "fs_set_fields from pinned host + fs_step_async(1) + fs_get_fields to pinned host, "
                        "wall clock"},
         "gpu_launches": r32["launches"],
         "clocks": clk.summary(),
-        "fp64": {"value": world * npts * args.steps / t64, "unit": UNIT, "ms_per_step": t64 * 1e3 / args.steps,
+        "fp64": {"value": job_value(world, npts, args.steps, t64), "unit": UNIT, "ms_per_step": t64 * 1e3 / args.steps,
                  "kernels_ms": r64["kern_ms"], "launches": r64["launches"]},
         "cufft_structure": cufft,
     }
