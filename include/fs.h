@@ -72,7 +72,7 @@ typedef enum {
 
 typedef enum {
   FS_SCHEME_SEMI_IMPLICIT_FS = 0, /* Algorithm 1 */
-  FS_SCHEME_EXPLICIT_FD = 1       /* Section 2.2 comparison scheme (2D only) */
+  FS_SCHEME_EXPLICIT_FD = 1       /* Section 2.2 comparison scheme (2D and 3D) */
 } fs_scheme;
 
 /* Problem description.  Physical parameters follow Section 2.1 (benchmark

@@ -1,12 +1,13 @@
 // Explicit finite-difference comparison scheme of Boccardo et al. (arXiv
 // 2306.04322, Section 2.2): forward Euler in time, second-order centred
-// 5-point Laplacian on a periodic 2D grid, three stages per step
+// 5-point (2D) / 7-point (3D) Laplacian on a periodic grid, three stages per
+// step
 //   (i)   mu    = df/dc - kappa_c lap(c)
 //   (ii)  c'    = c + dt M lap(mu)
 //   (iii) eta'_i = eta_i - dt L (df/deta_i - kappa_eta lap(eta_i))
-// fused into one kernel: a CTA loads a tile with a two-point halo (periodic
-// wrap instead of the paper's ghost layers), forms mu on the tile plus a
-// one-point halo in shared memory, then updates its interior.
+// In 2D fused into one kernel: a CTA loads a tile with a two-point halo
+// (periodic wrap instead of the paper's ghost layers), forms mu on the tile
+// plus a one-point halo in shared memory, then updates its interior.
 #include "fs_kernels.cuh"
 
 namespace fs {
@@ -29,7 +30,7 @@ __global__ void __launch_bounds__(FD_TX* FD_TY) fs_fd_kernel(KArgs a, const T* _
   for (int f = 0; f < nf; ++f)
     for (int i = tid; i < FD_WX * FD_WY; i += blockDim.x) {
       const int lx = i % FD_WX, ly = i / FD_WX;
-      const int gx = ((x0 + lx - 2) % nx + nx) % nx, gy = ((y0 + ly - 2) % ny + ny) % ny;
+      const int gx = (x0 + lx - 2) & (nx - 1), gy = (y0 + ly - 2) & (ny - 1);  // periodic (powers of two)
       tile[(f * FD_WY + ly) * FD_WX + lx] = in[f * N + (long long)gy * nx + gx];
     }
   __syncthreads();
@@ -78,8 +79,93 @@ __global__ void __launch_bounds__(FD_TX* FD_TY) fs_fd_kernel(KArgs a, const T* _
   if (bad) atomicOr(a.flag, FS_FLAG_NONFINITE);
 }
 
+// 3D: the same three stages with the 7-point Laplacian, as two kernels (one
+// thread per grid point, neighbours through the caches).  Kernel 1 forms mu
+// (stage i) into a scratch field and writes the updated eta_i (stage iii);
+// kernel 2 applies stage ii to c.  Axes are powers of two, so the periodic
+// neighbours are masks.
 template <typename T>
-cudaError_t fd_launch_t(const KArgs& a, const void* in, void* out, cudaStream_t s) {
+struct Grid3 {
+  int nx, ny, nz;
+  long long N;
+  int lx, lxy;  // log2(nx), log2(nx ny)
+  __device__ Grid3(const KArgs& a) : nx(a.nx), ny(a.ny), nz(a.nz), N(a.npts) {
+    lx = __ffs(nx) - 1;
+    lxy = lx + __ffs(ny) - 1;
+  }
+  __device__ __forceinline__ void coords(long long i, int& x, int& y, int& z) const {
+    x = (int)i & (nx - 1);
+    y = (int)(i >> lx) & (ny - 1);
+    z = (int)(i >> lxy);
+  }
+  __device__ __forceinline__ long long at(int x, int y, int z) const {
+    return ((long long)z * ny + y) * nx + x;
+  }
+  // 7-point Laplacian of field f at (x, y, z)
+  __device__ __forceinline__ T lap(const T* __restrict__ f, int x, int y, int z, T ix2, T iy2, T iz2) const {
+    const T c0 = f[at(x, y, z)];
+    return (f[at((x - 1) & (nx - 1), y, z)] - T(2) * c0 + f[at((x + 1) & (nx - 1), y, z)]) * ix2 +
+           (f[at(x, (y - 1) & (ny - 1), z)] - T(2) * c0 + f[at(x, (y + 1) & (ny - 1), z)]) * iy2 +
+           (f[at(x, y, (z - 1) & (nz - 1))] - T(2) * c0 + f[at(x, y, (z + 1) & (nz - 1))]) * iz2;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) fs_fd3_mu_eta_kernel(KArgs a, const T* __restrict__ in, T* __restrict__ out,
+                                                            T* __restrict__ mu) {
+  const Grid3<T> g(a);
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  int x, y, z;
+  g.coords(i, x, y, z);
+  const Pointwise<T> pw(a);
+  const Coef<T>& k = coef<T>(a);
+  const int nf = a.nf;
+  const T c = in[i];
+  T h = T(0), S2 = T(0);
+  for (int f = 1; f < nf; ++f) {
+    const T e = in[f * g.N + i];
+    h += pw.hpoly(e);
+    S2 += e * e;
+  }
+  mu[i] = pw.fc(c, h) - k.kc * g.lap(in, x, y, z, k.idx2, k.idy2, k.idz2);
+  bool bad = false;
+  for (int f = 1; f < nf; ++f) {
+    const T* ef = in + f * g.N;
+    const T e = ef[i];
+    const T en = e - k.dtL * (pw.feta(c, e, S2) - k.ke * g.lap(ef, x, y, z, k.idx2, k.idy2, k.idz2));
+    bad |= !finite_val(en);
+    out[f * g.N + i] = en;
+  }
+  if (bad) atomicOr(a.flag, FS_FLAG_NONFINITE);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) fs_fd3_c_kernel(KArgs a, const T* __restrict__ in, T* __restrict__ out,
+                                                       const T* __restrict__ mu) {
+  const Grid3<T> g(a);
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  int x, y, z;
+  g.coords(i, x, y, z);
+  const Coef<T>& k = coef<T>(a);
+  const T cn = in[i] + k.dtM * g.lap(mu, x, y, z, k.idx2, k.idy2, k.idz2);
+  if (!finite_val(cn)) atomicOr(a.flag, FS_FLAG_NONFINITE);
+  out[i] = cn;
+}
+
+template <typename T>
+cudaError_t fd_launch_t(const KArgs& a, const void* in, void* out, void* scratch, cudaStream_t s) {
+  if (a.nz > 1) {
+    const unsigned blocks = (unsigned)((a.npts + 255) / 256);
+    fs_fd3_mu_eta_kernel<T><<<blocks, 256, 0, s>>>(a, reinterpret_cast<const T*>(in), reinterpret_cast<T*>(out),
+                                                   reinterpret_cast<T*>(scratch));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    fs_fd3_c_kernel<T><<<blocks, 256, 0, s>>>(a, reinterpret_cast<const T*>(in), reinterpret_cast<T*>(out),
+                                              reinterpret_cast<const T*>(scratch));
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)((a.nx + FD_TX - 1) / FD_TX), (unsigned)((a.ny + FD_TY - 1) / FD_TY));
   size_t smem = sizeof(T) * ((size_t)a.nf * FD_WX * FD_WY + FD_MX * FD_MY);
   fs_fd_kernel<T><<<grid, FD_TX * FD_TY, smem, s>>>(a, reinterpret_cast<const T*>(in), reinterpret_cast<T*>(out));
@@ -88,8 +174,10 @@ cudaError_t fd_launch_t(const KArgs& a, const void* in, void* out, cudaStream_t 
 
 }  // namespace
 
-cudaError_t fd_launch(bool f64, const KArgs& a, const void* in, void* out, cudaStream_t s) {
-  return f64 ? fd_launch_t<double>(a, in, out, s) : fd_launch_t<float>(a, in, out, s);
+int fd_launches_per_step(const KArgs& a) { return a.nz > 1 ? 2 : 1; }
+
+cudaError_t fd_launch(bool f64, const KArgs& a, const void* in, void* out, void* scratch, cudaStream_t s) {
+  return f64 ? fd_launch_t<double>(a, in, out, scratch, s) : fd_launch_t<float>(a, in, out, scratch, s);
 }
 
 }  // namespace fs

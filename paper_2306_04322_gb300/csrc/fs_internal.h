@@ -112,7 +112,10 @@ int col_batch_tk_f64(int nx, int ny);
 size_t col_smem_f32(int ny, int tk);
 size_t col_smem_f64(int ny, int tk);
 // One explicit finite-difference step (fs_fd.cu): in -> out, nf fields each.
-cudaError_t fd_launch(bool f64, const KArgs& a, const void* in, void* out, cudaStream_t s);
+// Explicit FD step from `in` to `out` (nf real fields each); 3D needs an
+// N-real scratch field for mu that aliases neither.
+cudaError_t fd_launch(bool f64, const KArgs& a, const void* in, void* out, void* scratch, cudaStream_t s);
+int fd_launches_per_step(const KArgs& a);
 // FP64 sum of n values of x (float or double) added into *out.
 cudaError_t sum_launch_f32(const void* x, long long n, double* out, cudaStream_t s);
 cudaError_t sum_launch_f64(const void* x, long long n, double* out, cudaStream_t s);

@@ -350,7 +350,12 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
   // everything above only touched constant tables; the spectra are the
   // previous pass's output
   griddep_wait();
-  if (threadIdx.x == 0) row_issue<T, NX>(a, rb, slots, bar);
+  if (threadIdx.x == 0) {
+    // the ensemble kernel reuses the slots: order the previous item's
+    // generic accesses (ended by the CTA barrier above) before the copies
+    fence_proxy_async_smem();
+    row_issue<T, NX>(a, rb, slots, bar);
+  }
   griddep_launch_dependents();
   if (!mbar_wait_bounded(bar, parity, kWaitPolls)) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
@@ -457,6 +462,9 @@ __device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap
 
   if (threadIdx.x == 0) {
     griddep_wait();  // the tiles are the previous pass's output
+    // the ensemble kernel reuses the tiles: order the previous item's generic
+    // accesses (ended by the caller's CTA barrier) before the TMA writes
+    fence_proxy_async_smem();
     mbar_arrive_expect_tx(bar, (uint32_t)(nin * NY * tk * sizeof(C)));
     const int cx = kx0 * (int)(sizeof(C) / 8);  // innermost coordinate in 8-byte units
     for (int i = 0; i < nin; ++i) {

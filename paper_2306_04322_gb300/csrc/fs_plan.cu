@@ -155,10 +155,6 @@ fs_status validate(const fs_params* p, std::string* why) {
     *why = "3D grids support y and z axes up to 512";
     return FS_ERR_UNSUPPORTED;
   }
-  if (p->scheme == FS_SCHEME_EXPLICIT_FD && p->ndim != 2) {
-    *why = "the explicit FD comparison scheme is built for 2D grids";
-    return FS_ERR_UNSUPPORTED;
-  }
   if (p->precision == FS_F32_TC_TF32 || p->precision == FS_F32_TC_BF16X3) {
     if (p->scheme != FS_SCHEME_SEMI_IMPLICIT_FS || p->n[0] < 64 || p->n[1] < 64 ||
         (p->ndim > 2 && p->n[2] < 64)) {
@@ -342,6 +338,11 @@ int pass_kinds(const Member& m) { return m.prm.ndim > 2 ? 4 : 2; }
 cudaError_t launch_pass(const fs_plan* p, const Member& m, const fs::KArgs& a, int kind, cudaStream_t s);
 
 void* fd_buf(const Member& m, int which) { return which == 0 ? m.real : m.spec; }
+// mu scratch of the 3D explicit FD step: the spectrum buffer's last slot
+// (holds (nf + 1) N reals; the state uses the first nf N when it lives there)
+void* fd_scratch(const fs_plan* p, const Member& m) {
+  return (char*)m.spec + (size_t)(1 + m.prm.p) * m.npts * (p->f64 ? 8 : 4);
+}
 
 // Batched ensemble: kind 0 row pass (mode 0 from spectra, 1 from real
 // fields), kind 1 column pass, each one persistent launch for all members.
@@ -358,10 +359,10 @@ cudaError_t enqueue_step(fs_plan* p, int mode, cudaStream_t s, int64_t* launches
   if (p->fd) {
     for (Member& m : p->members) {
       fs::KArgs a = make_args(p, m, 0);
-      cudaError_t e = fs::fd_launch(p->f64, a, fd_buf(m, m.fd_cur), fd_buf(m, 1 - m.fd_cur), s);
+      cudaError_t e = fs::fd_launch(p->f64, a, fd_buf(m, m.fd_cur), fd_buf(m, 1 - m.fd_cur), fd_scratch(p, m), s);
       if (e != cudaSuccess) return e;
       m.fd_cur = 1 - m.fd_cur;
-      *launches += 1;
+      *launches += fs::fd_launches_per_step(a);
     }
     return cudaSuccess;
   }
@@ -1036,10 +1037,11 @@ fs_status fs_step_profiled(fs_plan_t p, int64_t nsteps) {
       for (Member& m : p->members) {
         fs::KArgs a = make_args(p, m, 0);
         rec(0);
-        if (e == cudaSuccess) e = fs::fd_launch(p->f64, a, fd_buf(m, m.fd_cur), fd_buf(m, 1 - m.fd_cur), p->stream);
+        if (e == cudaSuccess)
+          e = fs::fd_launch(p->f64, a, fd_buf(m, m.fd_cur), fd_buf(m, 1 - m.fd_cur), fd_scratch(p, m), p->stream);
         rec(0);
         m.fd_cur = 1 - m.fd_cur;
-        launches++;
+        launches += fs::fd_launches_per_step(a);
       }
     if (e != cudaSuccess) return cuda_fail(p, e, "fs_step_profiled");
     p->last_launches = launches;

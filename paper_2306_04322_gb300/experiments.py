@@ -2,6 +2,7 @@
 
     python -m paper_2306_04322_gb300.experiments precision   [--steps 2000]
     python -m paper_2306_04322_gb300.experiments accuracy    [--steps 10000]
+    python -m paper_2306_04322_gb300.experiments cost        [--steps 200]
 
 Both start from the benchmark initial condition of Section 3 (Eqs. ic_c,
 ic_eta with p = 2, dx = 1), made periodic as the paper does: the explicit FD
@@ -16,6 +17,10 @@ accuracy: 2D 1024^2, p = 2 (FP64): the semi-implicit FS step at dt = 6 dt_FD
     FD scheme (Section 2.2) at 0.95 dt_FD, all to the same end time, against
     a spectral FS reference at dt / 16; E_phi of Eq. (error_field) for c and
     for eta = sum_i eta_i, and the device time each run took.
+cost: device time per step of the FS step and of the explicit FD scheme on
+    the grid sizes of the paper's Tables 1 and 2 that fit here (2D 128^2 ..
+    1024^2, 3D 16^3 .. 256^3), p = 4 as in the paper, FP64 and FP32; the
+    ratio FS / FD is the paper's per-step cost comparison (Section 3).
 """
 from __future__ import annotations
 
@@ -114,17 +119,54 @@ def accuracy_study(steps: int):
     return res
 
 
+def _time_steps(fs, pr, precision, scheme, steps):
+    import torch
+    from . import inputs as I
+    dtype = torch.float64 if precision == "f64" else torch.float32
+    plan = fs.Plan(pr, precision, scheme=scheme)
+    plan.set_fields(torch.tensor(I.noise_fields(pr, seed=0), dtype=dtype, device="cuda"))
+    plan.step(max(3, steps // 10))  # warm-up (graph capture, caches)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    plan.close()
+    return ms
+
+
+def cost_study(steps: int):
+    from . import fs, inputs as I
+    rows = []
+    for n in [(128, 128), (256, 256), (512, 512), (1024, 1024), (16, 16, 16), (32, 32, 32), (64, 64, 64),
+              (128, 128, 128), (256, 256, 256)]:
+        pr = I.Problem(n=n, p=4)
+        pr.dt = 0.95 * I.fd_stable_dt(pr)
+        for prec in ("f64", "f32"):
+            k = steps if pr.npoints <= 1 << 21 else max(10, steps // 10)
+            fs_ms = _time_steps(fs, pr, prec, fs.FS_SCHEME_SEMI_IMPLICIT_FS, k)
+            fd_ms = _time_steps(fs, pr, prec, fs.FS_SCHEME_EXPLICIT_FD, k)
+            rows.append({"grid": list(n), "precision": prec, "steps": k, "fs_ms_per_step": fs_ms,
+                         "fd_ms_per_step": fd_ms, "fs_over_fd": fs_ms / fd_ms,
+                         "fs_gpts_per_s": pr.npoints / (fs_ms / 1e3)})
+    return {"workload": "p = 4 (5 fields), seeded +-0.01 noise, dt = 0.95 dt_FD for both schemes", "rows": rows}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2306_04322_gb300.experiments")
-    ap.add_argument("study", choices=["precision", "accuracy"])
+    ap.add_argument("study", choices=["precision", "accuracy", "cost"])
     ap.add_argument("--steps", type=int, default=None)
     args = ap.parse_args(argv)
     from . import build as B
     B.build()
     if args.study == "precision":
         out = precision_study(args.steps or 2000)
-    else:
+    elif args.study == "accuracy":
         out = accuracy_study(args.steps or 10000)
+    else:
+        out = cost_study(args.steps or 200)
     print(json.dumps(out))
 
 

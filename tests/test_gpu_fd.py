@@ -1,5 +1,6 @@
 """GPU parity of the explicit finite-difference comparison scheme (Section
-2.2: forward Euler, 5-point Laplacian, periodic) against the FP64 oracle."""
+2.2: forward Euler, 5-point (2D) / 7-point (3D) Laplacian, periodic) against
+the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -62,4 +63,23 @@ def test_fd_conserves_mean_c(F):
     pr.dt = 0.95 * I.fd_stable_dt(pr)
     f0 = I.noise_fields(pr, seed=10)
     out = run_fd(F, pr, f0, 333)
+    assert abs(out[0].mean() - f0[0].mean()) < 1e-13
+
+
+@pytest.mark.parametrize("n,p,dx", [((16, 16, 16), 2, (1.0, 1.0, 1.0)), ((32, 16, 8), 1, (1.0, 0.5, 2.0)),
+                                    ((8, 8, 8), 0, (1.0, 1.0, 1.0)), ((64, 32, 16), 4, (1.0, 1.0, 1.0))])
+def test_fd3_fp64_matches_oracle(F, O, n, p, dx):
+    pr = I.Problem(n=n, dx=dx, p=p)
+    pr.dt = 0.95 * I.fd_stable_dt(pr)
+    f0 = I.noise_fields(pr, seed=11)
+    assert rel_linf(run_fd(F, pr, f0, 1), O.fd_step(pr, f0, 1)) <= 1e-12
+    assert rel_linf(run_fd(F, pr, f0, 20), O.fd_step(pr, f0, 20)) <= 1e-10
+
+
+def test_fd3_fp32_and_mean(F, O):
+    pr = I.Problem(n=(32, 32, 32), p=2)
+    pr.dt = 0.95 * I.fd_stable_dt(pr)
+    f0 = I.noise_fields(pr, seed=12)
+    assert rel_linf(run_fd(F, pr, f0.astype(np.float32), 10, "f32"), O.fd_step(pr, f0, 10)) <= 1e-5
+    out = run_fd(F, pr, f0, 200)
     assert abs(out[0].mean() - f0[0].mean()) < 1e-13
