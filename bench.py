@@ -295,7 +295,7 @@ def extras(steps: int, warmup: int, device: int, peak, peak_kind):
     k = max(3, min(steps, 20))
     r = time_plan(pr, "f32", k, min(warmup, 3), device)
     nf, s, N = 1 + P, 4, r["npts"]
-    alg = [(2 * nf + 1) * N * s, 2 * (nf + 1) * N * s, (2 * nf + 1) * N * s, 2 * nf * N * s]
+    alg = [2 * nf * N * s, 2 * (nf + 1) * N * s, (2 * nf + 1) * N * s, 2 * nf * N * s]
     out["3d_256_p2_f32"] = {"value": N * k / (r["total_ms"] / 1e3), "unit": UNIT, "steps": k,
                             "ms_per_step": r["total_ms"] / k, "dt": pr.dt, "launches": r["launches"],
                             "workspace_bytes": r["workspace_bytes"],
@@ -306,7 +306,7 @@ def extras(steps: int, warmup: int, device: int, peak, peak_kind):
     kb = max(3, min(steps, 10))
     r = time_plan(probs, "f32", kb, min(warmup, 3), device)
     N = r["npts"]
-    alg = [(2 * nf + 1) * N * s, (2 * nf + 1) * N * s]
+    alg = [2 * nf * N * s, (2 * nf + 1) * N * s]
     out["batched_512_f32"] = {"value": N * kb / (r["total_ms"] / 1e3), "unit": UNIT, "steps": kb,
                               "ms_per_step": r["total_ms"] / kb, "members": 512, "points": N,
                               "launches": r["launches"], "schedule": {"row_grid": r["schedule"][0],
@@ -494,10 +494,10 @@ def main():
     s = 4
     nf = 1 + P
     names = ["fs_row_kernel", "fs_col_kernel"]
-    # algorithmic bytes per launch (steady state): row pass reads nf half
-    # spectra (nf N s bytes) and writes nf + 1 (2D, N/2 complex each);
-    # column pass reads nf + 1 and writes nf.
-    alg = [(2 * nf + 1) * npts * s, (2 * nf + 1) * npts * s]
+    # algorithmic bytes per launch (steady state): the row pass reads the nf
+    # carried half spectra (nf N s bytes: N/2 complex each) and writes nf
+    # (g_i and df/dc); the column pass reads nf + 1 and writes nf.
+    alg = [2 * nf * npts * s, (2 * nf + 1) * npts * s]
     avg_ms = [m / max(c, 1) for m, c in zip(r32["kern_ms"], r32["kern_cnt"])]
     dom = max(range(len(avg_ms)), key=lambda i: r32["kern_ms"][i])
     achieved = alg[dom] / (avg_ms[dom] / 1e3) / 1e9

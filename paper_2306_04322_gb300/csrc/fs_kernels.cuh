@@ -112,9 +112,11 @@ __device__ __forceinline__ bool finite_val(T x) {
 // mode 2: inverse only: spec slots 0..nf-1 -> real fields
 // mode 3: free-energy diagnostic: real fields in, sum of f_chem into acc[0],
 //         2 x^(phi) of every field into spec slots 0..nf-1
-// Outputs of a step: spec slot 0 = 2 x^(c), slots 1..p = 2 x^(g_i),
-// slot nf = 2 x^(df/dc) (x-spectra scaled by 2; the factor is folded into
-// the k-space scale).
+// Outputs of a step: slots 1..p = 2 x^(g_i), slot nf = 2 x^(df/dc) (x-spectra
+// scaled by 2; the factor is folded into the k-space scale); slot 0 = x^(c)
+// / nx, the scaling in which the column pass leaves the updated c, so in
+// mode 0 slot 0 is left as loaded (c^ is carried from step to step, as in
+// Algorithm 1) and only mode 1 writes it.
 // ---------------------------------------------------------------------------
 template <typename T, int NX>
 struct RowCfg {
@@ -207,7 +209,11 @@ __device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T
     // of c, g_1..g_p, df/dc (nf slots only for the diagnostic, mode 3); warp
     // w takes items w, w + nw, ...
     const int items = inv ? ((a.mode == 0 || a.mode == 2) ? nf : 0) : (a.mode == 3 ? nf : nf + 1);
-    for (int f = w; f < items; f += nw) {
+    // c's x spectrum is carried (Algorithm 1 keeps c^ from the previous
+    // step): in mode 0 the loaded slot 0 already holds it, so the forward
+    // phase starts at slot 1
+    const int f0 = (!inv && a.mode == 0) ? 1 : 0;
+    for (int f = f0 + w; f < items; f += nw) {
       C* s = slot(f, g);
       auto st = [s](int i, C v) { s[pad32(i)] = v; };
       auto ld = [s](int i) { return s[pad32(i)]; };
@@ -248,6 +254,8 @@ __device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T
         }
       } else {
         // packed half spectrum, scaled by 2, straight to global memory
+        const bool c_carried = (f == 0 && a.mode == 1);
+        const T c_scale = T(0.5) / T(a.nx);
         wsync();
 #pragma unroll
         for (int m = 0; m < E; ++m) s[t + TPL * m] = v[m];
@@ -266,6 +274,9 @@ __device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T
               const C A = cadd(zk, zm), B = csub(zk, zm);
               out = cadd(A, mul_i<-1>(cmul(B, wk(m))));
             }
+            // mode 1, c: store in the carried scaling, x spectrum / nx (what
+            // the column pass leaves behind), 2 x^ / (2 nx) (exact: power of 2)
+            if (c_carried) out = cscale(out, c_scale);
             P[k] = out;
           }
         }
@@ -409,19 +420,25 @@ struct ColCfg {
 
 template <typename T>
 struct KUpdate {
-  T Mdt, Mdtkc, Ldtke, scale;
+  T Mdt, Mdtkc, Ldtke, scale, Mdt_c, scale_c;
   __device__ explicit KUpdate(const KArgs& a) {
     const Coef<T>& k = coef<T>(a);
     Mdt = k.Mdt;
     Mdtkc = k.Mdtkc;
     Ldtke = k.Ldtke;
     scale = k.scale;
+    // c arrives in the carried scaling (x spectrum / nx, see the row pass)
+    // while df/dc arrives as 2 x^: fold the factor 2 nx into the
+    // coefficients (powers of two, so exact)
+    Mdt_c = Mdt * (T(0.5) / T(a.nx));
+    scale_c = scale * T(2 * a.nx);
   }
-  // c^' = (c^ - M dt K2 f^) / (1 + M dt kappa_c K2^2), times the 1/(2N) scale
+  // c^' = (c^ - M dt K2 f^) / (1 + M dt kappa_c K2^2), times the 1/(2N) scale;
+  // zc = c^ / (2 nx) in the units of zf
   template <typename C>
   __device__ __forceinline__ C c(C zc, C zf, T k2) const {
-    T d = scale / (T(1) + Mdtkc * k2 * k2);
-    T b = Mdt * k2;
+    T d = scale_c / (T(1) + Mdtkc * k2 * k2);
+    T b = Mdt_c * k2;
     return cscale(vfma(zf, vsplat<C>(-b), zc), d);
   }
   // eta^' = g^ / (1 + L dt kappa_eta K2), times the 1/(2N) scale

@@ -19,6 +19,9 @@ namespace {
 
 thread_local std::string g_thread_error;
 
+// Which buffers hold the current state: the real fields, the spectra (the
+// carried x spectra the next row pass starts from), or both (after
+// fs_get_fields, so reading the fields does not change the trajectory).
 enum StateKind { kStateNone = 0, kStateReal = 1, kStateSpec = 2, kStateBoth = 3 };
 
 struct Member {
@@ -876,7 +879,7 @@ fs_status fs_get_fields(fs_plan_t p, void* const* out) {
       cudaError_t e = launch_row(p, a, p->stream);
       if (e != cudaSuccess) return cuda_fail(p, e, "inverse row pass");
     }
-    p->state = kStateReal;
+    p->state = kStateBoth;  // the spectra stay valid: the next step carries on from them
   }
   const size_t rs = p->f64 ? sizeof(double) : sizeof(float);
   int idx = 0;
