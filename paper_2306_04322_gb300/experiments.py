@@ -59,16 +59,16 @@ def periodic_benchmark_state(fs, pr2d, t_end: float = 1.0):
     return out
 
 
-def precision_study(steps: int):
+def precision_study(steps: int, n: int = 256):
     import torch
     from . import fs, inputs as I
-    pr = I.Problem(n=(256, 256, 256), p=2)
+    pr = I.Problem(n=(n, n, n), p=2)
     pr.dt = 6.0 * I.fd_stable_dt(pr)
-    s2d = periodic_benchmark_state(fs, I.Problem(n=(256, 256), p=2)).cpu().numpy()
-    f0 = torch.tensor(I.extrude_3d(s2d, 256), dtype=torch.float64, device="cuda")
+    s2d = periodic_benchmark_state(fs, I.Problem(n=(n, n), p=2)).cpu().numpy()
+    f0 = torch.tensor(I.extrude_3d(s2d, n), dtype=torch.float64, device="cuda")
     del s2d
     ref, ms_ref = _run(fs, pr, f0, steps, "f64")
-    out = {"workload": "3D 256^3, p=2, dt=5e-3, benchmark IC at t=1 extruded along z (Eq. ic_eta_3d)",
+    out = {"workload": f"3D {n}^3, p=2, dt=5e-3, benchmark IC at t=1 extruded along z (Eq. ic_eta_3d)",
            "steps": steps,
            "initial_phase_fraction": [float((f0[1 + i] > 0.5).double().mean()) for i in range(pr.p)],
            "f64": {"ms_per_step": ms_ref / steps,
@@ -87,17 +87,17 @@ def error_field(ref, phi):
     return float(((ref - phi) ** 2).sum() / (ref ** 2).sum())
 
 
-def accuracy_study(steps: int):
+def accuracy_study(steps: int, n: int = 1024):
     import torch
     from . import fs, inputs as I
-    pr = I.Problem(n=(1024, 1024), p=2)
+    pr = I.Problem(n=(n, n), p=2)
     dt_fd = I.fd_stable_dt(pr)
     pr.dt = 6.0 * dt_fd
     t_end = steps * pr.dt
     f0 = periodic_benchmark_state(fs, pr)
     ref_pr = pr.replace(dt=pr.dt / 16)
     ref, ms_ref = _run(fs, ref_pr, f0, 16 * steps, "f64")
-    res = {"workload": "2D 1024^2, p=2, benchmark IC at t=1, FP64", "t_start": 1.0, "t_end": 1.0 + t_end,
+    res = {"workload": f"2D {n}^2, p=2, benchmark IC at t=1, FP64", "t_start": 1.0, "t_end": 1.0 + t_end,
            "reference": {"scheme": "FS", "dt": ref_pr.dt, "steps": 16 * steps, "ms": ms_ref}}
 
     def errs(g):
@@ -137,11 +137,14 @@ def _time_steps(fs, pr, precision, scheme, steps):
     return ms
 
 
-def cost_study(steps: int):
+COST_GRIDS = [(128, 128), (256, 256), (512, 512), (1024, 1024), (16, 16, 16), (32, 32, 32), (64, 64, 64),
+              (128, 128, 128), (256, 256, 256)]
+
+
+def cost_study(steps: int, grids=COST_GRIDS):
     from . import fs, inputs as I
     rows = []
-    for n in [(128, 128), (256, 256), (512, 512), (1024, 1024), (16, 16, 16), (32, 32, 32), (64, 64, 64),
-              (128, 128, 128), (256, 256, 256)]:
+    for n in grids:
         pr = I.Problem(n=n, p=4)
         pr.dt = 0.95 * I.fd_stable_dt(pr)
         for prec in ("f64", "f32"):
