@@ -49,7 +49,7 @@ def test_config5_adjoint_gradients(F, O):
         u0t = torch.tensor(u0, dtype=torch.float64 if prec == "f64" else torch.float32, device="cuda")
         loss = A.misfit_loss(A.trajectory(th, u0t, pr, prec, STEPS, EVERY), target)
         loss.backward()
-        grads[prec], losses[prec] = th.grad.numpy(), float(loss)
+        grads[prec], losses[prec] = th.grad.numpy(), float(loss.detach())
     fd = []
     u0t = torch.tensor(u0, device="cuda")
     for q in range(4):
