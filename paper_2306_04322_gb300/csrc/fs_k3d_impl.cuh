@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(LineCfg<T, NY>::THREADS, 4)
       // first radix-16 pass on tensor cores (input still in the tile), rest on CUDA cores
       static_assert(sizeof(T) == 4 && E == 16, "tensor-core stage: FP32, radix 16");
       float* bsm = reinterpret_cast<float*>(tile + Cfg::TROWS * tk);
-      tc_fill_b<TCM>(bsm);
+      tc_load_b(bsm, reinterpret_cast<const float*>(a.tc_b));
       __syncthreads();
       tc_first_pass16<NY, TCM>(reinterpret_cast<float2*>(tile), tk, bsm);
 #pragma unroll
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(LineCfg<T, NZ>::THREADS, 4)
   float* bsm = reinterpret_cast<float*>(tiles + 2 * TROWS * tk);
   if constexpr (TCM != TC_NONE) {
     static_assert(sizeof(T) == 4 && E == 16, "tensor-core stage: FP32, radix 16");
-    tc_fill_b<TCM>(bsm);
+    tc_load_b(bsm, reinterpret_cast<const float*>(a.tc_b));
     __syncthreads();
   }
   C v[E];

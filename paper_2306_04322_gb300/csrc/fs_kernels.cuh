@@ -510,7 +510,7 @@ __device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap
   float* bsm = reinterpret_cast<float*>(tiles + 2 * TROWS * tk);
   if constexpr (TCM != TC_NONE) {
     static_assert(sizeof(T) == 4 && E == 16, "tensor-core stage: FP32, radix 16");
-    tc_fill_b<TCM>(bsm);
+    tc_load_b(bsm, reinterpret_cast<const float*>(a.tc_b));
     __syncthreads();
   }
 

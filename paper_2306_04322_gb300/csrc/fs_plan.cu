@@ -37,6 +37,7 @@ struct Member {
   void* tw_col = nullptr;
   void* tw_z = nullptr;
   void* tw_half = nullptr;
+  void* tc_b = nullptr;  // split DFT matrix of the tensor-core stage (TC precisions)
   double* csum = nullptr;
   long long slot_stride = 0;
   CUtensorMap tmap_col;  // [slot * nz + z][y][kx] tiles of the 2D column pass / 3D y passes
@@ -240,6 +241,7 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   a.tw_col = m.tw_col;
   a.tw_z = m.tw_z;
   a.tw_half = m.tw_half;
+  a.tc_b = m.tc_b;
   a.k2x = m.k2x;
   a.k2y = m.k2y;
   a.k2z = m.k2z;
@@ -451,12 +453,87 @@ fs_status read_flag(fs_plan* p) {
 //   k2x[nx/2 + 1] | k2y[ny] | k2z[nz]        (real, padded to 16 bytes)
 //   tw_row | tw_col | tw_z                  (Stockham pass tables, complex)
 //   tw_half[nx/2]                           (exp(-2 pi i k / nx), complex)
+//   tc_b[2048] (TC precisions only)         (split DFT matrix of the tensor-core stage, 32-bit words)
 struct TableLayout {
-  size_t k2x, k2y, k2z, tw_row, tw_col, tw_z, tw_half, total;  // offsets in bytes
+  size_t k2x, k2y, k2z, tw_row, tw_col, tw_z, tw_half, tc_b, total;  // offsets in bytes
   int Lrow, Erow, Lcol, Ecol, Lz, Ez;
 };
 
 size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+// Tensor-core DFT stage of a precision (the device's TC mode numbers):
+// 0 none, 1 TF32 x 3, 2 BF16 x 3.
+constexpr int kTcTf32 = 1, kTcBf16 = 2;
+int tc_split(int precision) {
+  return precision == FS_F32_TC_TF32 ? kTcTf32 : precision == FS_F32_TC_BF16X3 ? kTcBf16 : 0;
+}
+
+// High half of a float in the split the tensor-core stage uses: TF32 (10
+// mantissa bits, round to nearest with ties away from zero, as the device's
+// cvt.rna.tf32.f32) or BF16 (7 mantissa bits, round to nearest even).
+float split_hi(float x, int mode) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if (mode == kTcTf32) {
+    u = (u + 0x1000u) & 0xFFFFE000u;
+  } else {
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    u &= 0xFFFF0000u;
+  }
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+// B = [[Wr, Wi], [-Wi, Wr]] (32 x 32; row kc = input index r, +16 for the
+// imaginary half; column nc = output index k, +16 for the imaginary half),
+// W[r][k] = exp(-2 pi i r k / 16), split into hi and lo halves and stored in
+// the MMA fragment order the device reads with one 16-byte load per lane:
+//   TF32 (m16n8k8):  [nn < 4][kk < 4][lane][hi(k0, nc), hi(k0 + 4, nc), lo(k0, nc), lo(k0 + 4, nc)],
+//                    k0 = 8 kk + lane % 4, nc = 8 nn + lane / 4;
+//   BF16 (m16n8k16): [nn < 4][kk < 2][lane][hi pair(k0), hi pair(k0 + 8), lo pair(k0), lo pair(k0 + 8)],
+//                    k0 = 16 kk + 2 (lane % 4), pair(k) = bf16(B[k][nc]) | bf16(B[k + 1][nc]) << 16.
+void tc_table(int mode, uint32_t* out) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  float hi[32][32], lo[32][32];
+  for (int kc = 0; kc < 32; ++kc)
+    for (int nc = 0; nc < 32; ++nc) {
+      const int r = kc & 15, pin = kc >> 4, k = nc & 15, pout = nc >> 4;
+      const long double ang = 2.0L * pi * (long double)((r * k) % 16) / 16.0L;
+      const double wr = (double)cosl(ang), wi = (double)-sinl(ang);
+      const double v = (pin == 0) ? (pout == 0 ? wr : wi) : (pout == 0 ? -wi : wr);
+      hi[kc][nc] = split_hi((float)v, mode);
+      lo[kc][nc] = split_hi((float)(v - (double)hi[kc][nc]), mode);
+    }
+  auto bits = [](float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    return u;
+  };
+  auto pair = [&](const float (&m)[32][32], int k, int nc) {
+    return (bits(m[k][nc]) >> 16) | (bits(m[k + 1][nc]) & 0xFFFF0000u);
+  };
+  const int nkk = mode == kTcTf32 ? 4 : 2;
+  for (int nn = 0; nn < 4; ++nn)
+    for (int kk = 0; kk < nkk; ++kk)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int nc = 8 * nn + lane / 4, t4 = lane % 4;
+        uint32_t* w = out + (((nn * nkk + kk) * 32 + lane) * 4);
+        if (mode == kTcTf32) {
+          const int k0 = 8 * kk + t4;
+          w[0] = bits(hi[k0][nc]);
+          w[1] = bits(hi[k0 + 4][nc]);
+          w[2] = bits(lo[k0][nc]);
+          w[3] = bits(lo[k0 + 4][nc]);
+        } else {
+          const int k0 = 16 * kk + 2 * t4;
+          w[0] = pair(hi, k0, nc);
+          w[1] = pair(hi, k0 + 8, nc);
+          w[2] = pair(lo, k0, nc);
+          w[3] = pair(lo, k0 + 8, nc);
+        }
+      }
+}
 
 TableLayout table_layout(const fs_params& prm, bool f64) {
   TableLayout t{};
@@ -483,6 +560,8 @@ TableLayout table_layout(const fs_params& prm, bool f64) {
   o = align16(o + cs * (nz > 1 ? fs::pass_table_size(t.Lz, t.Ez) : 0));
   t.tw_half = o;
   o = align16(o + cs * (nx / 2));
+  t.tc_b = o;
+  o = align16(o + (tc_split(prm.precision) ? 2048 * sizeof(float) : 0));
   t.total = o;
   return t;
 }
@@ -566,6 +645,10 @@ cudaError_t upload_tables(Member& m, bool f64, char* dev, size_t bytes) {
   m.tw_col = dev + t.tw_col;
   m.tw_z = dev + t.tw_z;
   m.tw_half = dev + t.tw_half;
+  if (const int mode = tc_split(prm.precision)) {
+    tc_table(mode, reinterpret_cast<uint32_t*>(buf.data() + t.tc_b));
+    m.tc_b = dev + t.tc_b;
+  }
   return cudaMemcpy(dev, buf.data(), bytes, cudaMemcpyHostToDevice);
 }
 

@@ -28,39 +28,13 @@ __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
   return r;
 }
 
-// cos / sin (2 pi m / 16), exact decimal constants through cos32
-__device__ __forceinline__ void cs16(int m, double& c, double& s) {
-  const int j = (2 * m) & 31;  // units of 2 pi / 32
-  const int q = j / 8, r = j % 8;
-  const double cr = cos32(r), sr = sin32(r);
-  if (q == 0) { c = cr; s = sr; }
-  else if (q == 1) { c = -sr; s = cr; }
-  else if (q == 2) { c = -cr; s = -sr; }
-  else { c = sr; s = -cr; }
-}
-
-// Fills the split DFT matrix B (hi and lo parts, [2][32][32] floats) in
-// shared memory; all threads of the CTA take part, no barrier inside.
-template <int MODE>
-__device__ __forceinline__ void tc_fill_b(float* bsm) {
-  for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
-    const int kc = idx >> 5, nc = idx & 31;
-    const int r = kc & 15, pin = kc >> 4, k = nc & 15, pout = nc >> 4;
-    double c, s;
-    cs16(r * k, c, s);  // W = c - i s
-    const double wr = c, wi = -s;
-    const double v = (pin == 0) ? (pout == 0 ? wr : wi) : (pout == 0 ? -wi : wr);
-    float hi, lo;
-    if (MODE == TC_TF32) {
-      hi = __uint_as_float(f32_to_tf32((float)v));
-      lo = __uint_as_float(f32_to_tf32((float)(v - (double)hi)));
-    } else {
-      hi = __bfloat162float(__float2bfloat16_rn((float)v));
-      lo = __bfloat162float(__float2bfloat16_rn((float)(v - (double)hi)));
-    }
-    bsm[idx] = hi;
-    bsm[1024 + idx] = lo;
-  }
+// Copies the split DFT matrix B into shared memory (all threads of the CTA,
+// no barrier inside).  The host stores it in fragment order: for every
+// (N tile nn, K tile kk) and lane, the four 32-bit words the lane passes to
+// its three MMAs (hi b0, hi b1, lo b0, lo b1; TF32 values, or pairs of BF16
+// values packed lower-k first), so one 16-byte load per (nn, kk) feeds them.
+__device__ __forceinline__ void tc_load_b(float* bsm, const float* __restrict__ tab) {
+  for (int idx = threadIdx.x; idx < 2048; idx += blockDim.x) bsm[idx] = __ldg(&tab[idx]);
 }
 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -93,6 +67,7 @@ template <int NL, int MODE>
 __device__ __forceinline__ void tc_first_pass16(float2* tile, int tk, const float* bsm) {
   constexpr int NB = NL / 16;  // butterflies per column
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ltk = __ffs(tk) - 1;  // tk is a power of two
   const int g = lane >> 2, t4 = lane & 3;
   // The thread's A-fragment columns r (input index of the radix-16 DFT):
   //   TF32 (m16n8k8):  r = t4 + 4 sl;             BF16 (m16n8k16): r = 2 t4 + (sl & 1) + 8 (sl >> 1)
@@ -104,7 +79,7 @@ __device__ __forceinline__ void tc_first_pass16(float2* tile, int tk, const floa
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int row = mt * 16 + g + 8 * h;
-      const int b = row / tk, j = row % tk;
+      const int b = row >> ltk, j = row & (tk - 1);
 #pragma unroll
       for (int sl = 0; sl < 4; ++sl) {
         const float2 x = tile[(b + NB * rof(sl)) * tk + j];
@@ -151,29 +126,22 @@ __device__ __forceinline__ void tc_first_pass16(float2* tile, int tk, const floa
 #pragma unroll
     for (int nn = 0; nn < 4; ++nn) {
       float d[4] = {0.f, 0.f, 0.f, 0.f};
-      const int nc = nn * 8 + g;
+      const uint4* bq = reinterpret_cast<const uint4*>(bsm);
       if (MODE == TC_TF32) {
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-          const int k0 = kk * 8 + t4;
-          const uint32_t bh0 = __float_as_uint(bsm[k0 * 32 + nc]), bh1 = __float_as_uint(bsm[(k0 + 4) * 32 + nc]);
-          const uint32_t bl0 = __float_as_uint(bsm[1024 + k0 * 32 + nc]);
-          const uint32_t bl1 = __float_as_uint(bsm[1024 + (k0 + 4) * 32 + nc]);
-          mma_tf32(d, alo[kk], bh0, bh1);
-          mma_tf32(d, ahi[kk], bl0, bl1);
-          mma_tf32(d, ahi[kk], bh0, bh1);
+          const uint4 bf = bq[(nn * 4 + kk) * 32 + lane];
+          mma_tf32(d, alo[kk], bf.x, bf.y);
+          mma_tf32(d, ahi[kk], bf.z, bf.w);
+          mma_tf32(d, ahi[kk], bf.x, bf.y);
         }
       } else {
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
-          const int k0 = kk * 16 + 2 * t4;
-          const uint32_t bh0 = pack_bf16(bsm[k0 * 32 + nc], bsm[(k0 + 1) * 32 + nc]);
-          const uint32_t bh1 = pack_bf16(bsm[(k0 + 8) * 32 + nc], bsm[(k0 + 9) * 32 + nc]);
-          const uint32_t bl0 = pack_bf16(bsm[1024 + k0 * 32 + nc], bsm[1024 + (k0 + 1) * 32 + nc]);
-          const uint32_t bl1 = pack_bf16(bsm[1024 + (k0 + 8) * 32 + nc], bsm[1024 + (k0 + 9) * 32 + nc]);
-          mma_bf16(d, alo[kk], bh0, bh1);
-          mma_bf16(d, ahi[kk], bl0, bl1);
-          mma_bf16(d, ahi[kk], bh0, bh1);
+          const uint4 bf = bq[(nn * 2 + kk) * 32 + lane];
+          mma_bf16(d, alo[kk], bf.x, bf.y);
+          mma_bf16(d, ahi[kk], bf.z, bf.w);
+          mma_bf16(d, ahi[kk], bf.x, bf.y);
         }
       }
       // D fragment: (g, 2t4), (g, 2t4+1), (g+8, 2t4), (g+8, 2t4+1)
@@ -182,7 +150,7 @@ __device__ __forceinline__ void tc_first_pass16(float2* tile, int tk, const floa
         const int row = row0 + 8 * (e >> 1);
         const int ncol = nn * 8 + 2 * t4 + (e & 1);
         const int k = ncol & 15;
-        const int b = row / tk, j = row % tk;
+        const int b = row >> ltk, j = row & (tk - 1);
         const int q = 16 * b + k;
         float* dst = reinterpret_cast<float*>(&tile[(q + (q >> 4)) * tk + j]);
         dst[ncol >> 4] = d[e];
