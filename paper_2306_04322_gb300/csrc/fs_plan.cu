@@ -878,18 +878,33 @@ fs_status fs_batch_create(const fs_params* each, int count, void* stream, fs_pla
   return create_common(each, count, stream, nullptr, nullptr, nullptr, out);
 }
 
+// Copies nf fields of n bytes each between the plan's contiguous field block
+// `dev` and the caller's nf pointers; runs of caller pointers that are
+// themselves contiguous go in one copy.
+cudaError_t copy_fields(char* dev, const void* const* ptrs, int nf, size_t n, bool to_dev, cudaStream_t s) {
+  for (int f = 0; f < nf;) {
+    int g = f + 1;
+    while (g < nf && (const char*)ptrs[g] == (const char*)ptrs[g - 1] + n) ++g;
+    cudaError_t e = to_dev ? cudaMemcpyAsync(dev + f * n, ptrs[f], (g - f) * n, cudaMemcpyDefault, s)
+                           : cudaMemcpyAsync(const_cast<void*>(ptrs[f]), dev + f * n, (g - f) * n,
+                                             cudaMemcpyDefault, s);
+    if (e != cudaSuccess) return e;
+    f = g;
+  }
+  return cudaSuccess;
+}
+
 fs_status fs_set_fields(fs_plan_t p, const void* const* fields) {
   if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
   if (!fields) return fail(p, FS_ERR_INVALID_ARG, "fields is NULL");
   const size_t rs = p->f64 ? sizeof(double) : sizeof(float);
+  for (size_t i = 0; i < p->members.size() * p->nf; ++i)
+    if (!fields[i]) return fail(p, FS_ERR_INVALID_ARG, "field pointer is NULL");
   int idx = 0;
   for (Member& m : p->members) {
-    for (int f = 0; f < p->nf; ++f, ++idx) {
-      if (!fields[idx]) return fail(p, FS_ERR_INVALID_ARG, "field pointer is NULL");
-      char* dst = (char*)m.real + (size_t)f * m.npts * rs;
-      cudaError_t e = cudaMemcpyAsync(dst, fields[idx], m.npts * rs, cudaMemcpyDefault, p->stream);
-      if (e != cudaSuccess) return cuda_fail(p, e, "fs_set_fields copy");
-    }
+    cudaError_t ec = copy_fields((char*)m.real, fields + idx, p->nf, m.npts * rs, true, p->stream);
+    if (ec != cudaSuccess) return cuda_fail(p, ec, "fs_set_fields copy");
+    idx += p->nf;
     m.fd_cur = 0;
     if (!p->f64 && !p->fd) {
       cudaError_t e = cudaMemsetAsync(m.csum, 0, sizeof(double), p->stream);
@@ -965,14 +980,15 @@ fs_status fs_get_fields(fs_plan_t p, void* const* out) {
     p->state = kStateBoth;  // the spectra stay valid: the next step carries on from them
   }
   const size_t rs = p->f64 ? sizeof(double) : sizeof(float);
+  for (size_t i = 0; i < p->members.size() * p->nf; ++i)
+    if (!out[i]) return fail(p, FS_ERR_INVALID_ARG, "output pointer is NULL");
   int idx = 0;
-  for (const Member& m : p->members)
-    for (int f = 0; f < p->nf; ++f, ++idx) {
-      if (!out[idx]) return fail(p, FS_ERR_INVALID_ARG, "output pointer is NULL");
-      const char* src = (const char*)(p->fd ? fd_buf(m, m.fd_cur) : m.real) + (size_t)f * m.npts * rs;
-      cudaError_t e = cudaMemcpyAsync(out[idx], src, m.npts * rs, cudaMemcpyDefault, p->stream);
-      if (e != cudaSuccess) return cuda_fail(p, e, "fs_get_fields copy");
-    }
+  for (const Member& m : p->members) {
+    char* src = (char*)(p->fd ? fd_buf(m, m.fd_cur) : m.real);
+    cudaError_t e = copy_fields(src, out + idx, p->nf, m.npts * rs, false, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "fs_get_fields copy");
+    idx += p->nf;
+  }
   cudaError_t e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return cuda_fail(p, e, "stream synchronize");
   return FS_OK;
