@@ -1,6 +1,8 @@
 // Launch dispatch for the 2D row / column kernels of one precision.
 #pragma once
 
+#include <type_traits>
+
 #include "fs_kernels.cuh"
 
 namespace fs {
@@ -152,11 +154,27 @@ int col_tk_t(int nx, int ny) {
 }
 
 // FP64 sum reduction (grid-stride, warp shuffles, one atomic per CTA).
-template <typename T>
+// VEC: 16-byte vector loads (x 16-byte aligned, n a multiple of 16 / sizeof(T)).
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(256) fs_sum_kernel(const T* __restrict__ x, long long n, double* out) {
   double s = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    s += (double)x[i];
+  if constexpr (VEC) {
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int W = 16 / sizeof(T);
+    const V* __restrict__ xv = reinterpret_cast<const V*>(x);
+    const long long nv = n / W;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv;
+         i += (long long)gridDim.x * blockDim.x) {
+      const V v = __ldg(&xv[i]);
+      if constexpr (W == 4)
+        s += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
+      else
+        s += (double)v.x + (double)v.y;
+    }
+  } else {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+      s += (double)x[i];
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   __shared__ double ws[8];
@@ -171,10 +189,15 @@ __global__ void __launch_bounds__(256) fs_sum_kernel(const T* __restrict__ x, lo
 
 template <typename T>
 cudaError_t sum_launch_t(const void* x, long long n, double* out, cudaStream_t s) {
-  long long blocks = (n + 255) / 256;
-  if (blocks > 1216) blocks = 1216;
+  const long long W = 16 / (long long)sizeof(T);
+  const bool vec = ((uintptr_t)x % 16 == 0) && (n % W == 0);
+  long long blocks = ((vec ? n / W : n) + 255) / 256;
+  if (blocks > 608) blocks = 608;
   if (blocks < 1) blocks = 1;
-  fs_sum_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const T*>(x), n, out);
+  if (vec)
+    fs_sum_kernel<T, true><<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const T*>(x), n, out);
+  else
+    fs_sum_kernel<T, false><<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const T*>(x), n, out);
   return cudaGetLastError();
 }
 
