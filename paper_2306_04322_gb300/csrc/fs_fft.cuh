@@ -275,10 +275,15 @@ __device__ __forceinline__ void line_fft(C (&v)[E], int t, const C* __restrict__
   stockham<L, E, 1, DIR>(v, t, twp, st, ld, sync);
 }
 
-// Padded shared-memory index: one spare slot every 32 elements keeps the
-// stride-R butterfly writes and the stride-TPL reads free of bank conflicts.
+// Padded shared-memory indices: one spare slot every 32 (pad32) or 16
+// (pad16) elements.  pad16 keeps the radix-16 butterfly writes (16
+// consecutive elements per thread) and the stride-TPL reads of the row
+// exchanges free of bank conflicts for 8-byte elements (each half-warp is
+// served separately).
 __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 constexpr int padded_len(int L) { return L + L / 32 + 1; }
+constexpr int padded16_len(int L) { return L + L / 16 + 1; }
 
 // Cooperative copy of n complex values global -> shared (all threads).
 template <typename C>
