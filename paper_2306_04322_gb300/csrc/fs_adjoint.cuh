@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(192) fs_adj_row_fwd_kernel(KArgs a) {
   C* spec = reinterpret_cast<C*>(a.spec);
   for (int o = w; o < 3 * nf; o += nw) {
     C* s = slot(o, g);
-    auto st = [s](int i, C v) { s[pad16(i)] = v; };
-    auto ld = [s](int i) { return s[pad16(i)]; };
+    auto st = [s](int i, C v) { s[Cfg::P16 ? pad16(i) : pad32(i)] = v; };
+    auto ld = [s](int i) { return s[Cfg::P16 ? pad16(i) : pad32(i)]; };
     C v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = s[t + TPL * m];
@@ -354,8 +354,8 @@ __global__ void __launch_bounds__(192) fs_adj_row_inv_kernel(KArgs a) {
   }
   for (int o = w; o < 2 * nf; o += nw) {
     C* s = slot(o, g);
-    auto st = [s](int i, C v) { s[pad16(i)] = v; };
-    auto ld = [s](int i) { return s[pad16(i)]; };
+    auto st = [s](int i, C v) { s[Cfg::P16 ? pad16(i) : pad32(i)] = v; };
+    auto ld = [s](int i) { return s[Cfg::P16 ? pad16(i) : pad32(i)]; };
     C v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {

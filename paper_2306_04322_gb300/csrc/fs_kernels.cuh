@@ -106,7 +106,8 @@ __device__ __forceinline__ bool finite_val(T x) {
 //   phase 2 all threads: pointwise stage, df/dc into slot nf, g_i over eta_i;
 //   phase 3 warp o <= nf: forward x transform of slot o to global memory.
 // Slot contents use the natural layout (element i at i) except during the
-// FFT exchanges, which use the padded layout (element i at pad16(i)).
+// FFT exchanges, which use a padded layout (element i at pad16(i) or pad32(i),
+// see RowCfg).
 // mode 0: step, previous state in spec slots 0..nf-1 (y-inverted spectra)
 // mode 1: step, previous state in the real fields
 // mode 2: inverse only: spec slots 0..nf-1 -> real fields
@@ -125,11 +126,15 @@ struct RowCfg {
   static constexpr int E = row_E(L, F64);
   static constexpr int TPL = L / E;
   static constexpr int R = row_R(L, F64);                 // rows per CTA
-  // Slot pitch (complex): room for the pad16 layout, even so that every slot
-  // is 16-byte aligned for the bulk copies, and with R > 1 lines per warp
-  // = TPL (mod 16): the lines of a half-warp then start on different banks,
-  // which keeps the natural and the exchange accesses conflict-free.
-  static constexpr int PL0 = (padded16_len(L) + 1) & ~1;
+  // Exchange layout: pad16 when a warp holds several lines (R > 1), which
+  // with the pitch below makes the radix-16 writes and the stride-TPL
+  // accesses of 8-byte elements bank-conflict free; a warp holding one line
+  // keeps pad32 (fewer index instructions, conflicts already rare).
+  static constexpr bool P16 = R > 1;
+  // Slot pitch (complex): room for the layout, even so that every slot is
+  // 16-byte aligned for the bulk copies, and with R > 1 = TPL (mod 16), so
+  // the lines of a half-warp start on different banks.
+  static constexpr int PL0 = ((P16 ? padded16_len(L) : padded_len(L)) + 1) & ~1;
   static constexpr int PL = (R > 1 && TPL >= 2) ? PL0 + ((TPL - PL0 % 16) + 16) % 16 : PL0;
   static constexpr int THREADS = 4 * 32;                // four warps; warp w takes fields w, w + 4, ...
   static constexpr int MIN_BLOCKS = F64 ? 3 : 7;
@@ -215,8 +220,8 @@ __device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T
     const int f0 = (!inv && a.mode == 0) ? 1 : 0;
     for (int f = f0 + w; f < items; f += nw) {
       C* s = slot(f, g);
-      auto st = [s](int i, C v) { s[pad16(i)] = v; };
-      auto ld = [s](int i) { return s[pad16(i)]; };
+      auto st = [s](int i, C v) { s[Cfg::P16 ? pad16(i) : pad32(i)] = v; };
+      auto ld = [s](int i) { return s[Cfg::P16 ? pad16(i) : pad32(i)]; };
       C v[E];
       if (inv) {
         // half-length complex sequence of the real row from its packed half
