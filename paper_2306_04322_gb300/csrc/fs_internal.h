@@ -35,6 +35,7 @@ struct KArgs {
   const void* tw_row;      // pass tables of the x line FFT (L = nx/2)
   const void* tw_col;      // pass tables of the y line FFT (L = ny)
   const void* tw_z;        // pass tables of the z line FFT (L = nz, 3D)
+  const void* tw_row_w;    // pass tables of the x line FFT with 32 values per thread (FP32, nx = 1024; NULL: none)
   const void* tw_half;     // exp(-2 pi i k / nx), k = 0..nx/2-1 (real <-> half-length complex)
   const void* tc_b;        // tensor-core DFT stage: split 16-point DFT matrix, [hi | lo][32][32] float
   const void* k2x;         // |xi_x|^2 per x bin, nx/2 + 1 entries

@@ -40,15 +40,26 @@ cudaError_t launch_pdl(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+template <typename T, int NX, bool W>
+cudaError_t row_launch_w(const KArgs& a, cudaStream_t s) {
+  using Cfg = RowCfg<T, NX, W>;
+  const long long reff = a.lines < Cfg::R ? a.lines : Cfg::R;
+  const size_t smem = row_smem_bytes<T, NX, W>(a.nf);
+  static unsigned done = 0;
+  cudaError_t e = allow_big_smem(fs_row_kernel<T, NX, W>, &done);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(fs_row_kernel<T, NX, W>, dim3((unsigned)(a.lines / reff)), dim3((unsigned)Cfg::THREADS), smem, s,
+                    a);
+}
+
+// FP32 rows of 1024 take the wide (radix 32, 16) variant when the plan
+// provides its table.
 template <typename T, int NX>
 cudaError_t row_launch_n(const KArgs& a, cudaStream_t s) {
-  using Cfg = RowCfg<T, NX>;
-  const long long reff = a.lines < Cfg::R ? a.lines : Cfg::R;
-  const size_t smem = row_smem_bytes<T, NX>(a.nf);
-  static unsigned done = 0;
-  cudaError_t e = allow_big_smem(fs_row_kernel<T, NX>, &done);
-  if (e != cudaSuccess) return e;
-  return launch_pdl(fs_row_kernel<T, NX>, dim3((unsigned)(a.lines / reff)), dim3((unsigned)Cfg::THREADS), smem, s, a);
+  if constexpr (sizeof(T) == 4 && NX == 1024) {
+    if (a.tw_row_w) return row_launch_w<T, NX, true>(a, s);
+  }
+  return row_launch_w<T, NX, false>(a, s);
 }
 
 template <typename T, int NY>

@@ -119,13 +119,16 @@ __device__ __forceinline__ bool finite_val(T x) {
 // mode 0 slot 0 is left as loaded (c^ is carried from step to step, as in
 // Algorithm 1) and only mode 1 writes it.
 // ---------------------------------------------------------------------------
-template <typename T, int NX>
+// W: the wide variant, E = 32 values per thread (radix 32 then 16 for
+// L = 512: two passes, one exchange), used by plans for FP32 rows of 1024
+// with the plan's second pass table (KArgs::tw_row_w).
+template <typename T, int NX, bool W = false>
 struct RowCfg {
   static constexpr bool F64 = sizeof(T) == 8;
   static constexpr int L = NX / 2;
-  static constexpr int E = row_E(L, F64);
+  static constexpr int E = W ? 32 : row_E(L, F64);
   static constexpr int TPL = L / E;
-  static constexpr int R = row_R(L, F64);                 // rows per CTA
+  static constexpr int R = 32 / TPL;                       // rows per CTA
   // Exchange layout: pad16 when a warp holds several lines (R > 1), which
   // with the pitch below makes the radix-16 writes and the stride-TPL
   // accesses of 8-byte elements bank-conflict free; a warp holding one line
@@ -137,25 +140,25 @@ struct RowCfg {
   static constexpr int PL0 = ((P16 ? padded16_len(L) : padded_len(L)) + 1) & ~1;
   static constexpr int PL = (R > 1 && TPL >= 2) ? PL0 + ((TPL - PL0 % 16) + 16) % 16 : PL0;
   static constexpr int THREADS = 4 * 32;                // four warps; warp w takes fields w, w + 4, ...
-  static constexpr int MIN_BLOCKS = F64 ? 3 : 7;
+  static constexpr int MIN_BLOCKS = F64 ? 3 : (W ? 4 : 7);
   static constexpr int BAR_BYTES = 128;
   static constexpr int TWS = pass_table_size(L, E);  // twiddle entries (complex)
   static constexpr int TW_BYTES = ((TWS * (int)sizeof(cplx<T>)) + 127) & ~127;
 };
 
 // Shared memory of one row-pass CTA (bytes).
-template <typename T, int NX>
+template <typename T, int NX, bool W = false>
 constexpr size_t row_smem_bytes(int nf) {
-  return RowCfg<T, NX>::BAR_BYTES + RowCfg<T, NX>::TW_BYTES +
-         (size_t)(nf + 1) * RowCfg<T, NX>::R * RowCfg<T, NX>::PL * sizeof(cplx<T>);
+  using Cfg = RowCfg<T, NX, W>;
+  return Cfg::BAR_BYTES + Cfg::TW_BYTES + (size_t)(nf + 1) * Cfg::R * Cfg::PL * sizeof(cplx<T>);
 }
 
 // Issues the bulk-async copies of row block rb (every field's rows) into
 // the input slots `in` ([nf][R][PL]), completion on `bar`.  One thread only.
-template <typename T, int NX>
+template <typename T, int NX, bool W = false>
 __device__ __forceinline__ void row_issue(const KArgs& a, long long rb, cplx<T>* in, uint64_t* bar) {
   using C = cplx<T>;
-  using Cfg = RowCfg<T, NX>;
+  using Cfg = RowCfg<T, NX, W>;
   constexpr int L = Cfg::L, R = Cfg::R, PL = Cfg::PL;
   const int nf = a.nf;
   const int Reff = a.lines < R ? (int)a.lines : R;
@@ -175,11 +178,11 @@ __device__ __forceinline__ void row_issue(const KArgs& a, long long rb, cplx<T>*
 // Compute part of one row-pass work item (row block rb) once its rows have
 // landed: input slots `in` ([nf][R][PL], fields in natural layout), scratch
 // slot `scr` ([R][PL], df/dc), pass tables `twr` in shared memory.
-template <typename T, int NX>
+template <typename T, int NX, bool W = false>
 __device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T>* in, cplx<T>* scr,
                                             const cplx<T>* twr) {
   using C = cplx<T>;
-  using Cfg = RowCfg<T, NX>;
+  using Cfg = RowCfg<T, NX, W>;
   constexpr int L = Cfg::L, E = Cfg::E, TPL = Cfg::TPL, R = Cfg::R, PL = Cfg::PL;
   const int nf = a.nf;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -196,10 +199,12 @@ __device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T
   auto slot = [in, scr, nf](int f, int r) { return f < nf ? in + (f * R + r) * PL : scr + r * PL; };
   // Twiddles of the real <-> half-length complex step, W_k = exp(-2 pi i k / (2L))
   // for k = t + TPL m: W_t (one table entry) times the exact constant
-  // exp(-2 pi i m / (2E)), 2E <= 32.
-  static_assert(2 * E <= 32, "half-step twiddle constants need 2E <= 32");
+  // exp(-2 pi i m / (2E)) when 2E <= 32, else the table entry of k.
   const C wt = __ldg(&twh[t]);
-  auto wk = [wt](int m) { return twiddle_small<-1>(wt, m, 2 * E); };
+  auto wk = [wt, twh, t](int m) {
+    if constexpr (2 * E <= 32) return twiddle_small<-1>(wt, m, 2 * E);
+    else return __ldg(&twh[t + TPL * m]);
+  };
 
   // Both transform phases share one FFT call site (small instruction
   // footprint); the inverse is computed as conj(FFT(conj(.))).
@@ -354,14 +359,14 @@ __device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T
 // One row-pass work item with its own table copy and load (ensemble kernel):
 // `bar` is an initialised mbarrier whose next phase has parity `parity`.
 // Returns false if a bounded wait gave up (the caller must stop).
-template <typename T, int NX>
+template <typename T, int NX, bool W = false>
 __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned char* smem_raw, uint64_t* bar,
                                          uint32_t parity) {
   using C = cplx<T>;
-  using Cfg = RowCfg<T, NX>;
+  using Cfg = RowCfg<T, NX, W>;
   C* twr = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);
   C* slots = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES + Cfg::TW_BYTES);  // [(nf + 1) * R][PL]
-  copy_to_smem(twr, reinterpret_cast<const C*>(a.tw_row), Cfg::TWS);
+  copy_to_smem(twr, reinterpret_cast<const C*>(W ? a.tw_row_w : a.tw_row), Cfg::TWS);
   __syncthreads();
   // everything above only touched constant tables; the spectra are the
   // previous pass's output
@@ -370,7 +375,7 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
     // the ensemble kernel reuses the slots: order the previous item's
     // generic accesses (ended by the CTA barrier above) before the copies
     fence_proxy_async_smem();
-    row_issue<T, NX>(a, rb, slots, bar);
+    row_issue<T, NX, W>(a, rb, slots, bar);
   }
   griddep_launch_dependents();
   if (!mbar_wait_bounded(bar, parity, kWaitPolls)) {
@@ -378,13 +383,13 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
     mbar_wait_bounded(bar, parity, kWaitPolls);  // let the copies land before exiting
     return false;
   }
-  row_compute<T, NX>(a, rb, slots, slots + a.nf * Cfg::R * Cfg::PL, twr);
+  row_compute<T, NX, W>(a, rb, slots, slots + a.nf * Cfg::R * Cfg::PL, twr);
   return true;
 }
 
 
-template <typename T, int NX>
-__global__ void __launch_bounds__(RowCfg<T, NX>::THREADS, RowCfg<T, NX>::MIN_BLOCKS)
+template <typename T, int NX, bool W = false>
+__global__ void __launch_bounds__(RowCfg<T, NX, W>::THREADS, RowCfg<T, NX, W>::MIN_BLOCKS)
     fs_row_kernel(KArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -393,7 +398,7 @@ __global__ void __launch_bounds__(RowCfg<T, NX>::THREADS, RowCfg<T, NX>::MIN_BLO
     fence_mbar_init();
   }
   __syncthreads();
-  row_body<T, NX>(a, blockIdx.x, smem_raw, bar, 0);
+  row_body<T, NX, W>(a, blockIdx.x, smem_raw, bar, 0);
 }
 
 // ---------------------------------------------------------------------------

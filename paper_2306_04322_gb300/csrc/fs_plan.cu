@@ -37,6 +37,7 @@ struct Member {
   void* tw_col = nullptr;
   void* tw_z = nullptr;
   void* tw_half = nullptr;
+  void* tw_row_w = nullptr;  // x-pass tables with 32 values per thread (FP32 rows of 1024)
   void* tc_b = nullptr;  // split DFT matrix of the tensor-core stage (TC precisions)
   double* csum = nullptr;
   long long slot_stride = 0;
@@ -241,6 +242,7 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   a.tw_col = m.tw_col;
   a.tw_z = m.tw_z;
   a.tw_half = m.tw_half;
+  a.tw_row_w = m.tw_row_w;
   a.tc_b = m.tc_b;
   a.k2x = m.k2x;
   a.k2y = m.k2y;
@@ -455,7 +457,7 @@ fs_status read_flag(fs_plan* p) {
 //   tw_half[nx/2]                           (exp(-2 pi i k / nx), complex)
 //   tc_b[2048] (TC precisions only)         (split DFT matrix of the tensor-core stage, 32-bit words)
 struct TableLayout {
-  size_t k2x, k2y, k2z, tw_row, tw_col, tw_z, tw_half, tc_b, total;  // offsets in bytes
+  size_t k2x, k2y, k2z, tw_row, tw_row_w, tw_col, tw_z, tw_half, tc_b, total;  // offsets in bytes
   int Lrow, Erow, Lcol, Ecol, Lz, Ez;
 };
 
@@ -535,6 +537,9 @@ void tc_table(int mode, uint32_t* out) {
       }
 }
 
+// Rows of 1024 in FP32 run the x-pass variant with 32 values per thread.
+bool wide_rows(const fs_params& prm, bool f64) { return !f64 && prm.n[0] == 1024; }
+
 TableLayout table_layout(const fs_params& prm, bool f64) {
   TableLayout t{};
   const size_t rs = f64 ? 8 : 4, cs = 2 * rs;
@@ -554,6 +559,8 @@ TableLayout table_layout(const fs_params& prm, bool f64) {
   o = align16(o + rs * nz);
   t.tw_row = o;
   o = align16(o + cs * fs::pass_table_size(t.Lrow, t.Erow));
+  t.tw_row_w = o;  // wide x-pass variant (32 values per thread): FP32 rows of 1024
+  o = align16(o + (wide_rows(prm, f64) ? cs * fs::pass_table_size(t.Lrow, 32) : 0));
   t.tw_col = o;
   o = align16(o + cs * fs::pass_table_size(t.Lcol, t.Ecol));
   t.tw_z = o;
@@ -611,8 +618,9 @@ cudaError_t upload_tables(Member& m, bool f64, char* dev, size_t bytes) {
   for (int k = 0; k <= nx / 2; ++k) kx[k] = axis_k2(prm.lap, k, nx, prm.dx[0]);
   for (int k = 0; k < ny; ++k) ky[k] = axis_k2(prm.lap, k, ny, prm.dx[1]);
   for (int k = 0; k < nz && prm.ndim > 2; ++k) kz[k] = axis_k2(prm.lap, k, nz, prm.dx[2]);
-  std::vector<long double> rr, ii, cr, ci, zr, zi, hr, hi;
+  std::vector<long double> rr, ii, wr, wi, cr, ci, zr, zi, hr, hi;
   pass_table(t.Lrow, t.Erow, rr, ii);
+  if (wide_rows(prm, f64)) pass_table(t.Lrow, 32, wr, wi);
   pass_table(t.Lcol, t.Ecol, cr, ci);
   if (nz > 1) pass_table(t.Lz, t.Ez, zr, zi);
   const long double pi = 3.141592653589793238462643383279502884L;
@@ -634,6 +642,7 @@ cudaError_t upload_tables(Member& m, bool f64, char* dev, size_t bytes) {
     put_real<float>(buf, t.k2y, ky);
     put_real<float>(buf, t.k2z, kz);
     put_cplx<float>(buf, t.tw_row, rr, ii);
+    put_cplx<float>(buf, t.tw_row_w, wr, wi);
     put_cplx<float>(buf, t.tw_col, cr, ci);
     put_cplx<float>(buf, t.tw_z, zr, zi);
     put_cplx<float>(buf, t.tw_half, hr, hi);
@@ -642,6 +651,7 @@ cudaError_t upload_tables(Member& m, bool f64, char* dev, size_t bytes) {
   m.k2y = dev + t.k2y;
   m.k2z = dev + t.k2z;
   m.tw_row = dev + t.tw_row;
+  m.tw_row_w = wide_rows(prm, f64) ? dev + t.tw_row_w : nullptr;
   m.tw_col = dev + t.tw_col;
   m.tw_z = dev + t.tw_z;
   m.tw_half = dev + t.tw_half;

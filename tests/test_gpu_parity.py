@@ -97,6 +97,19 @@ def test_fp32_one_step(F, O, n, p):
     assert err <= 2e-6, err
 
 
+@pytest.mark.parametrize("n,p", [((1024, 64), 2), ((1024, 16, 16), 1)])
+def test_fp32_1024_rows_several_steps(F, O, n, p):
+    """FP32 rows of 1024 run the x-pass variant with 32 values per thread;
+    several steps exercise its steady state (carried spectra) and the final
+    inverse pass, against the FP64 oracle."""
+    pr = I.Problem(n=n, p=p)
+    pr.dt = 6.0 * I.fd_stable_dt(pr)
+    f0 = I.noise_fields(pr, seed=3)
+    ref, _ = O.step(pr, f0, 10)
+    err = rel_linf(gpu_run(F, pr, f0.astype(np.float32), 10, "f32"), ref)
+    assert err <= 1e-5, err
+
+
 def test_fp32_mean_carried_in_fp64(F):
     """FP32 plans carry sum(c) in FP64: mean(c) stays at its initial value to
     FP32 rounding of one inverse transform, with no drift over 500 steps."""
