@@ -295,7 +295,8 @@ def extras(steps: int, warmup: int, device: int, peak, peak_kind):
     k = max(3, min(steps, 20))
     r = time_plan(pr, "f32", k, min(warmup, 3), device)
     nf, s, N = 1 + P, 4, r["npts"]
-    alg = [2 * nf * N * s, 2 * (nf + 1) * N * s, (2 * nf + 1) * N * s, 2 * nf * N * s]
+    # x 2 nf (c^ carried), y forward 2 nf (c stays in (kx, ky, z) space), z 2 nf + 1, y inverse 2 nf
+    alg = [2 * nf * N * s, 2 * nf * N * s, (2 * nf + 1) * N * s, 2 * nf * N * s]
     out["3d_256_p2_f32"] = {"value": N * k / (r["total_ms"] / 1e3), "unit": UNIT, "steps": k,
                             "ms_per_step": r["total_ms"] / k, "dt": pr.dt, "launches": r["launches"],
                             "workspace_bytes": r["workspace_bytes"],

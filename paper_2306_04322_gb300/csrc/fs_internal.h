@@ -47,6 +47,9 @@ struct KArgs {
   long long lines;         // rows handled by a row pass (ny * nz)
   int mode;                // row pass: 0 step from spectra, 1 step from real, 2 inverse only
   int tc;                  // FP32 column transforms: 0 CUDA cores, 1 TF32 x 3, 2 BF16 x 3 tensor-core stage
+  int carry3;              // 3D FS: c stays in slot 0 as (kx, ky, z) spectrum between steps; its x spectrum
+                           // for the x pass goes to slot nf (see the 3D passes)
+  int plane0;              // y pass: first plane (slot * nz + z) of the launch
   double M, L, kappa_c, kappa_eta, rho2, c_alpha, c_beta, w, alpha, dt;
   double scale;            // k-space scale 1 / (2 N)
   double inv_npts;         // 1 / N

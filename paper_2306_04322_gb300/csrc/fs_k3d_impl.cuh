@@ -2,10 +2,17 @@
 // Algorithm 1 for 3D domains).  A step is four passes over the packed
 // x-spectra [slot][z][y][kx] (kx < nx/2, bin 0 = DC + i Nyquist):
 //   x pass     the 2D row kernel with ny * nz rows;
-//   y forward  fs_ypass_kernel<DIR = -1> on every slot (c, g_i, df/dc);
+//   y forward  fs_ypass_kernel<DIR = -1> on the slots g_i, df/dc (and c in
+//              the first step after the fields are set);
 //   z step     fs_zstep_kernel: forward z transform, k-space update with
 //              K2 = |xi_x|^2 + |xi_y|^2 + |xi_z|^2, inverse z transform;
 //   y inverse  fs_ypass_kernel<DIR = +1> on slots c, g_i.
+// c is carried between steps as Algorithm 1 carries c^: the z step leaves
+// c's (kx, ky, z) spectrum in slot 0 and the y inverse writes c's x spectrum
+// to slot nf (df/dc is consumed by then) instead of over it, so the next
+// step's x pass reads c from slot nf, its y forward skips slot 0, and its
+// z step finds c's (kx, ky, z) spectrum in slot 0 (a factor ny smaller than
+// the y forward would give: folded into the update).
 // The packed kx = 0 / Nyquist column of every z plane is split in the
 // y passes into the y-spectra A (x-DC) and B (x-Nyquist), each Hermitian in
 // ky, and stored as
@@ -55,7 +62,9 @@ __global__ void __launch_bounds__(LineCfg<T, NY>::THREADS, 4)
   const int j = threadIdx.x % tk, t = threadIdx.x / tk;
   const int Lh = a.nx / 2;
   const int kx0 = blockIdx.x * tk;
-  const int plane = blockIdx.y;  // slot * nz + z
+  const int plane = blockIdx.y + a.plane0;  // slot * nz + z
+  // y inverse of c with the 3D carry: c's x spectrum goes to slot nf
+  const int oplane = (DIR > 0 && a.carry3 && plane < a.nz) ? plane + a.nf * a.nz : plane;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -155,7 +164,7 @@ __global__ void __launch_bounds__(LineCfg<T, NY>::THREADS, 4)
       }
     }
   }
-  C* S = reinterpret_cast<C*>(a.spec) + (long long)plane * NY * Lh + kx0 + j;
+  C* S = reinterpret_cast<C*>(a.spec) + (long long)oplane * NY * Lh + kx0 + j;
 #pragma unroll
   for (int m = 0; m < E; ++m) S[(long long)(t + TPL * m) * Lh] = v[m];
 }

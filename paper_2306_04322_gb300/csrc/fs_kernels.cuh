@@ -170,7 +170,9 @@ __device__ __forceinline__ void row_issue(const KArgs& a, long long rb, cplx<T>*
   mbar_arrive_expect_tx(bar, bytes * Reff * nf);
   for (int f = 0; f < nf; ++f) {
     // the R rows of field f are contiguous in global memory
-    const C* src = from_real ? realc + f * (a.npts / 2) + row0 * L : spec + f * a.slot_stride + row0 * L;
+    // 3D carry: c's x spectrum sits in slot nf (see the 3D passes)
+    const int sl = (f == 0 && a.carry3) ? nf : f;
+    const C* src = from_real ? realc + f * (a.npts / 2) + row0 * L : spec + sl * a.slot_stride + row0 * L;
     for (int r = 0; r < Reff; ++r) bulk_g2s(in + (f * R + r) * PL, src + r * L, bytes, bar);
   }
 }
@@ -439,9 +441,12 @@ struct KUpdate {
     scale = k.scale;
     // c arrives in the carried scaling (x spectrum / nx, see the row pass)
     // while df/dc arrives as 2 x^: fold the factor 2 nx into the
-    // coefficients (powers of two, so exact)
-    Mdt_c = Mdt * (T(0.5) / T(a.nx));
-    scale_c = scale * T(2 * a.nx);
+    // coefficients (powers of two, so exact).  3D steady state: c comes
+    // straight from the previous z step, without the y inverse / forward
+    // round trip that would multiply it by ny: fold that in too.
+    const T q = (a.carry3 && a.mode == 0) ? T(2 * a.nx) * T(a.ny) : T(2 * a.nx);
+    Mdt_c = Mdt / q;
+    scale_c = scale * q;
   }
   // c^' = (c^ - M dt K2 f^) / (1 + M dt kappa_c K2^2), times the 1/(2N) scale;
   // zc = c^ / (2 nx) in the units of zf

@@ -256,6 +256,8 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   a.lines = (long long)a.ny * a.nz;
   a.mode = mode;
   a.tc = m.prm.precision == FS_F32_TC_TF32 ? 1 : (m.prm.precision == FS_F32_TC_BF16X3 ? 2 : 0);
+  a.carry3 = (m.prm.ndim == 3 && m.prm.scheme == FS_SCHEME_SEMI_IMPLICIT_FS) ? 1 : 0;
+  a.plane0 = 0;
   a.M = m.prm.M;
   a.L = m.prm.L;
   a.kappa_c = m.prm.kappa_c;
@@ -396,9 +398,15 @@ cudaError_t launch_pass(const fs_plan* p, const Member& m, const fs::KArgs& a, i
   if (kind == 0) return launch_row(p, a, s);
   if (m.prm.ndim == 2) return launch_col(p, m, a, s);
   const int nf = p->nf;
-  if (kind == 1)
-    return p->f64 ? fs::ypass_launch_f64(a, m.tmap_col, -1, nf + 1, s)
-                  : fs::ypass_launch_f32(a, m.tmap_col, -1, nf + 1, s);
+  if (kind == 1) {
+    // with c carried (steady state) the y forward skips slot 0
+    fs::KArgs b = a;
+    const bool skip_c = a.carry3 && a.mode == 0;
+    b.plane0 = skip_c ? a.nz : 0;
+    const int nslots = skip_c ? nf : nf + 1;
+    return p->f64 ? fs::ypass_launch_f64(b, m.tmap_col, -1, nslots, s)
+                  : fs::ypass_launch_f32(b, m.tmap_col, -1, nslots, s);
+  }
   if (kind == 2) return p->f64 ? fs::zstep_launch_f64(a, m.tmap_z, s) : fs::zstep_launch_f32(a, m.tmap_z, s);
   return p->f64 ? fs::ypass_launch_f64(a, m.tmap_col, 1, nf, s) : fs::ypass_launch_f32(a, m.tmap_col, 1, nf, s);
 }
