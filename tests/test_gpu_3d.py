@@ -80,3 +80,25 @@ def test_fp32_3d_mean_conserved(F):
     m0 = f0[0].astype(np.float64).mean()
     got = gpu_run(F, pr, f0, 200, "f32")
     assert abs(got[0].mean() - m0) <= 2e-7
+
+
+def test_3d_reading_fields_does_not_perturb_the_run(F, O):
+    """3D carries c between steps in (kx, ky, z) space and keeps c's x spectrum
+    in the df/dc slot: reading the fields between steps leaves the run bit for
+    bit unchanged, and the run matches the oracle."""
+    import torch
+    pr = I.Problem(n=(32, 16, 64), p=2, dx=(1.0, 0.5, 1.0))
+    pr.dt = 5.0 * I.fd_stable_dt(pr)
+    f0 = torch.tensor(I.noise_fields(pr, seed=21), device="cuda")
+    plan = F.Plan(pr, "f64")
+    plan.set_fields(f0)
+    plan.step(12)
+    full = plan.get_fields().cpu().numpy()
+    plan.set_fields(f0)
+    plan.step(5)
+    plan.get_fields()
+    plan.step(7)
+    assert np.array_equal(full, plan.get_fields().cpu().numpy())
+    plan.close()
+    ref, _ = O.step(pr, f0.cpu().numpy(), 12)
+    assert rel_linf(full, ref) <= 1e-11
