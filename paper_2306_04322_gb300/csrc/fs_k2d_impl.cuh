@@ -115,6 +115,7 @@ cudaError_t energy_col_launch_t(const KArgs& a, const CUtensorMap& tm, cudaStrea
     case 256: return energy_col_launch_n<T, 256>(a, tm, s);
     case 512: return energy_col_launch_n<T, 512>(a, tm, s);
     case 1024: return energy_col_launch_n<T, 1024>(a, tm, s);
+    case 2048: return energy_col_launch_n<T, 2048>(a, tm, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -130,6 +131,7 @@ cudaError_t row_launch_t(const KArgs& a, cudaStream_t s) {
     case 256: return row_launch_n<T, 256>(a, s);
     case 512: return row_launch_n<T, 512>(a, s);
     case 1024: return row_launch_n<T, 1024>(a, s);
+    case 2048: return row_launch_n<T, 2048>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -145,6 +147,7 @@ cudaError_t col_launch_t(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) 
     case 256: return col_launch_n<T, 256>(a, tm, s);
     case 512: return col_launch_n<T, 512>(a, tm, s);
     case 1024: return col_launch_n<T, 1024>(a, tm, s);
+    case 2048: return col_launch_n<T, 2048>(a, tm, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -160,6 +163,7 @@ int col_tk_t(int nx, int ny) {
     case 256: return col_tk_n<T, 256>(nx);
     case 512: return col_tk_n<T, 512>(nx);
     case 1024: return col_tk_n<T, 1024>(nx);
+    case 2048: return col_tk_n<T, 2048>(nx);
     default: return 0;
   }
 }

@@ -140,7 +140,9 @@ struct RowCfg {
   static constexpr int PL0 = ((P16 ? padded16_len(L) : padded_len(L)) + 1) & ~1;
   static constexpr int PL = (R > 1 && TPL >= 2) ? PL0 + ((TPL - PL0 % 16) + 16) % 16 : PL0;
   static constexpr int THREADS = 4 * 32;                // four warps; warp w takes fields w, w + 4, ...
-  static constexpr int MIN_BLOCKS = F64 ? 3 : (W ? 4 : 7);
+  // 32 values per thread (wide rows, rows of 2048) need about twice the
+  // registers of 16
+  static constexpr int MIN_BLOCKS = F64 ? (E >= 32 ? 2 : 3) : (E >= 32 ? 4 : 7);
   static constexpr int BAR_BYTES = 128;
   static constexpr int TWS = pass_table_size(L, E);  // twiddle entries (complex)
   static constexpr int TW_BYTES = ((TWS * (int)sizeof(cplx<T>)) + 127) & ~127;

@@ -152,12 +152,12 @@ fs_status validate(const fs_params* p, std::string* why) {
     return FS_ERR_INVALID_ARG;
   }
   for (int d = 0; d < p->ndim; ++d)
-    if (!pow2_in(p->n[d], 8, 1024)) {
-      *why = "each grid axis must be a power of two in [8, 1024]";
+    if (!pow2_in(p->n[d], 8, 2048)) {
+      *why = "each grid axis must be a power of two in [8, 2048]";
       return FS_ERR_UNSUPPORTED;
     }
-  if (p->ndim == 3 && (p->n[1] > 512 || p->n[2] > 512)) {
-    *why = "3D grids support y and z axes up to 512";
+  if (p->ndim == 3 && (p->n[0] > 1024 || p->n[1] > 512 || p->n[2] > 512)) {
+    *why = "3D grids support a power of two up to 1024 along x and up to 512 along y and z";
     return FS_ERR_UNSUPPORTED;
   }
   if (p->precision == FS_F32_TC_TF32 || p->precision == FS_F32_TC_BF16X3) {
@@ -682,8 +682,9 @@ fs_status setup_batch(fs_plan* p) {
       return fail(nullptr, FS_ERR_UNSUPPORTED, "batched plans hold 2D semi-implicit FS members");
     const int nx = m.prm.n[0], ny = m.prm.n[1];
     const int tk = p->f64 ? fs::col_batch_tk_f64(nx, ny) : fs::col_batch_tk_f32(nx, ny);
-    if (nx < 16 || tk == 0)
-      return fail(nullptr, FS_ERR_UNSUPPORTED, "batched members need nx >= 16 and ny >= 128 (FP32) / 64 (FP64)");
+    if (nx < 16 || nx > 1024 || ny > 1024 || tk == 0)
+      return fail(nullptr, FS_ERR_UNSUPPORTED,
+                  "batched members need 16 <= nx <= 1024 and ny in [128 (FP32) / 64 (FP64), 1024]");
     if (m.prm.precision == FS_F32_TC_TF32 || m.prm.precision == FS_F32_TC_BF16X3)
       return fail(nullptr, FS_ERR_UNSUPPORTED, "batched plans use the CUDA-core transforms (FS_F64 or FS_F32)");
   }
@@ -1079,6 +1080,8 @@ fs_status fs_step_adjoint(fs_plan_t p, const void* const* u, const void* const* 
   Member& m = p->members[0];
   if (p->members.size() != 1 || p->fd || m.prm.ndim != 2)
     return fail(p, FS_ERR_UNSUPPORTED, "fs_step_adjoint is built for single 2D semi-implicit FS plans");
+  if (m.prm.n[0] > 1024 || m.prm.n[1] > 1024)
+    return fail(p, FS_ERR_UNSUPPORTED, "fs_step_adjoint supports axes up to 1024");
   const size_t rs = p->f64 ? sizeof(double) : sizeof(float), cs = 2 * rs;
   const int nf = p->nf;
   if (!m.aspec) {

@@ -70,7 +70,7 @@ def test_invalid_params_rejected_without_cuda(L, field, value, status):
     assert L.fs_last_error(None)
 
 
-@pytest.mark.parametrize("n", [(48, 64), (64, 4), (2048, 64), (64, 12)])
+@pytest.mark.parametrize("n", [(48, 64), (64, 4), (4096, 64), (64, 12)])
 def test_unsupported_sizes(L, n):
     P = good_params()
     P.n[0], P.n[1] = n
@@ -120,3 +120,17 @@ def test_allocation_failure_reported_as_oom(L):
     assert st == F.FS_ERR_OOM
     assert calls["alloc"] >= 1 and h.value is None
     assert b"allocation" in L.fs_last_error(None)
+
+
+def test_3d_axis_limits(L):
+    """2D plans take axes up to 2048; 3D plans stop at 1024 along x and 512
+    along y and z."""
+    P = good_params()
+    P.ndim = 3
+    P.n[0], P.n[1], P.n[2] = 2048, 64, 64
+    P.dx[2] = 1.0
+    h = ctypes.c_void_p()
+    assert L.fs_plan_create(ctypes.byref(P), None, ctypes.byref(h)) == F.FS_ERR_UNSUPPORTED
+    assert b"3D grids" in L.fs_last_error(None)
+    P.n[0], P.n[1] = 64, 1024
+    assert L.fs_plan_create(ctypes.byref(P), None, ctypes.byref(h)) == F.FS_ERR_UNSUPPORTED
