@@ -286,8 +286,9 @@ def roofline_entry(names, alg_bytes, r, peak, peak_kind, traffic_table=None):
 
 
 def extras(steps: int, warmup: int, device: int, peak, peak_kind):
-    """3D 256^3 (p = 2, FP32) and the 512-member ensemble (FP32): throughput
-    and per-pass rooflines, reported beside the headline."""
+    """3D 256^3 (p = 2, FP32), 2D 2048^2 (p = 4, FP32) and the 512-member
+    ensemble (FP32): throughput and per-pass rooflines, reported beside the
+    headline."""
     from paper_2306_04322_gb300 import inputs as I
     out = {}
     pr = I.Problem(n=(256, 256, 256), p=P)
@@ -303,6 +304,18 @@ def extras(steps: int, warmup: int, device: int, peak, peak_kind):
                             "roofline": roofline_entry(["x_pass(fs_row_kernel)", "fs_ypass_kernel<-1>",
                                                         "fs_zstep_kernel", "fs_ypass_kernel<+1>"],
                                                        alg, r, peak, peak_kind, "traffic_3d_256_p2.txt")}
+    # the finest 2D grid of the paper's Table 1 with its five fields (p = 4)
+    pr = I.Problem(n=(2048, 2048), p=4)
+    pr.dt = 6.0 * I.fd_stable_dt(pr)
+    k = max(3, min(steps, 20))
+    r = time_plan(pr, "f32", k, min(warmup, 3), device)
+    nf4, N = 1 + pr.p, r["npts"]
+    out["2d_2048_p4_f32"] = {"value": N * k / (r["total_ms"] / 1e3), "unit": UNIT, "steps": k,
+                             "ms_per_step": r["total_ms"] / k, "dt": pr.dt, "launches": r["launches"],
+                             "workspace_bytes": r["workspace_bytes"],
+                             "roofline": roofline_entry(["fs_row_kernel", "fs_col_kernel"],
+                                                        [2 * nf4 * N * s, (2 * nf4 + 1) * N * s], r, peak,
+                                                        peak_kind)}
     probs = I.batch_problems(512, seed=0)
     kb = max(3, min(steps, 10))
     r = time_plan(probs, "f32", kb, min(warmup, 3), device)

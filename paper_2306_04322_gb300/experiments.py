@@ -3,10 +3,12 @@
     python -m paper_2306_04322_gb300.experiments precision   [--steps 2000]
     python -m paper_2306_04322_gb300.experiments accuracy    [--steps 10000]
     python -m paper_2306_04322_gb300.experiments cost        [--steps 200]
+    python -m paper_2306_04322_gb300.experiments table1      [--t-span 1]
 
-Both start from the benchmark initial condition of Section 3 (Eqs. ic_c,
-ic_eta with p = 2, dx = 1), made periodic as the paper does: the explicit FD
-scheme, run in FP64 on the GPU at half its stable dt, takes it to t = 1.
+precision and accuracy start from the benchmark initial condition of
+Section 3 (Eqs. ic_c, ic_eta with p = 2, dx = 1), made periodic as the paper
+does: the explicit FD scheme, run in FP64 on the GPU at half its stable dt,
+takes it to t = 1 (table1 does the same on the paper's 200 x 200 domain).
 
 precision: 3D 256^3, p = 2, dt = 5e-3: the t = 1 state of the 256^2 problem
     extruded along z (Eq. ic_eta_3d, c = c0); FP32, TF32 x 3 and BF16 x 3 runs
@@ -18,9 +20,12 @@ accuracy: 2D 1024^2, p = 2 (FP64): the semi-implicit FS step at dt = 6 dt_FD
     a spectral FS reference at dt / 16; E_phi of Eq. (error_field) for c and
     for eta = sum_i eta_i, and the device time each run took.
 cost: device time per step of the FS step and of the explicit FD scheme on
-    the grid sizes of the paper's Tables 1 and 2 that fit here (2D 128^2 ..
-    1024^2, 3D 16^3 .. 256^3), p = 4 as in the paper, FP64 and FP32; the
+    the grid sizes of the paper's Tables 1 and 2 (2D 128^2 .. 2048^2,
+    3D 16^3 .. 256^3), p = 4 as in the paper, FP64 and FP32; the
     ratio FS / FD is the paper's per-step cost comparison (Section 3).
+table1: the paper's 2D accuracy study (Table 1 grids and time steps,
+    domain 200, p = 4, E_phi against spectral FS FP64 on 2048^2 at
+    dt = 1e-4) over t = 1 -> 1 + t_span; see table1_study.
 """
 from __future__ import annotations
 
@@ -46,13 +51,23 @@ def _run(fs, pr, f0, steps, precision, scheme=None):
     return out, ms
 
 
+def ac_stable_dt(pr) -> float:
+    """Forward-Euler bound of the Allen-Cahn equations linearised with
+    eta_j <= 1: dt = 2 / (L (kappa_eta lambda + 2 w (1 + 2 alpha (p - 1)))),
+    lambda = sum_d 4 / dx_d^2; below the Cahn-Hilliard bound of
+    inputs.fd_stable_dt except on coarse grids (dx of a few units)."""
+    lam = sum(4.0 / (d * d) for d in pr.dx)
+    return 2.0 / (pr.L * (pr.kappa_eta * lam + 2.0 * pr.w * (1.0 + 2.0 * pr.alpha * max(pr.p - 1, 0))))
+
+
 def periodic_benchmark_state(fs, pr2d, t_end: float = 1.0):
     """Benchmark initial condition (Section 3) advanced to t_end by the
-    explicit FD scheme in FP64 at half its stable dt; an (nf, ny, nx) float64
-    CUDA tensor."""
+    explicit FD scheme in FP64 at half its stable dt (the smaller of the
+    Cahn-Hilliard and Allen-Cahn bounds); an (nf, ny, nx) float64 CUDA
+    tensor."""
     import torch
     from . import inputs as I
-    n = int(np.ceil(t_end / (0.5 * I.fd_stable_dt(pr2d))))
+    n = int(np.ceil(t_end / (0.5 * min(I.fd_stable_dt(pr2d), ac_stable_dt(pr2d)))))
     pre = pr2d.replace(dt=t_end / n)
     f0 = torch.tensor(I.benchmark_ic_fields(pr2d), dtype=torch.float64, device="cuda")
     out, _ = _run(fs, pre, f0, n, "f64", scheme=fs.FS_SCHEME_EXPLICIT_FD)
@@ -137,7 +152,7 @@ def _time_steps(fs, pr, precision, scheme, steps):
     return ms
 
 
-COST_GRIDS = [(128, 128), (256, 256), (512, 512), (1024, 1024), (16, 16, 16), (32, 32, 32), (64, 64, 64),
+COST_GRIDS = [(128, 128), (256, 256), (512, 512), (1024, 1024), (2048, 2048), (16, 16, 16), (32, 32, 32), (64, 64, 64),
               (128, 128, 128), (256, 256, 256)]
 
 
@@ -157,10 +172,108 @@ def cost_study(steps: int, grids=COST_GRIDS):
     return {"workload": "p = 4 (5 fields), seeded +-0.01 noise, dt = 0.95 dt_FD for both schemes", "rows": rows}
 
 
+# Table 1 of the paper: grids and time steps of the 2D accuracy study; the
+# explicit FD time steps are the paper's own (stable, below the linearised
+# bound of inputs.fd_stable_dt).
+TABLE1_GRIDS = (128, 256, 512, 1024, 2048)
+TABLE1_FS_DTS = (1e-4, 1e-3, 5e-3)
+TABLE1_FD_DT = {128: 8.138e-3, 256: 5.086e-4, 512: 3.560e-5, 1024: 2.225e-6, 2048: 1.490e-7}
+
+
+def spectral_resample(f: np.ndarray, n: int) -> np.ndarray:
+    """Periodic fields (..., m, m) on an n x n grid of the same domain by
+    Fourier interpolation: the modes |k_x|, |k_y| < min(m, n) / 2 are kept
+    (the Nyquist bins are dropped, so the result is real) and the rest are
+    zero.  For n >= m every grid receives the same band-limited field; for
+    n < m the field is truncated to what the coarse grid represents.  Input
+    preparation only (host numpy), not part of the time step."""
+    m = f.shape[-1]
+    F = np.fft.fft2(f, axes=(-2, -1))
+    h = min(m, n) // 2
+    idx = np.r_[0:h, -h + 1:0]
+    out = np.zeros(f.shape[:-2] + (n, n), dtype=complex)
+    out[..., idx[:, None], idx[None, :]] = F[..., idx[:, None], idx[None, :]]
+    return np.real(np.fft.ifft2(out, axes=(-2, -1))) * (n * n) / (m * m)
+
+
+def table1_study(t_span: float = 1.0, grids=TABLE1_GRIDS, dts=TABLE1_FS_DTS, ref_dt: float = 1e-4,
+                 pre_n: int = 512, l: float = 200.0, p: int = 4, precision: str = "f64", fd_dts=None,
+                 fd_max_steps: int = 100_000):
+    """The 2D accuracy study of Section 3 (Table 1, Eq. error_field) over a
+    shortened time window.
+
+    Setting of the paper: domain 200 x 200, p = 4, the benchmark initial
+    condition made periodic by the explicit FD scheme up to t = 1 (here on a
+    pre_n^2 grid in FP64 at half its stable dt), the same t = 1 state on
+    every grid (spectral_resample), then t = 1 -> 1 + t_span with the FS
+    scheme (spectral |xi|^2 and the FS-FD O(dl^2) / O(dl^4) forms) at every
+    (grid, dt) of Table 1, and with the explicit FD scheme at the paper's FD
+    dt where that takes at most fd_max_steps steps.  Reference: spectral FS
+    in FP64 on the finest grid at ref_dt (the paper's choice: 2048^2, 1e-4);
+    the sweep case equal to it is the reference run itself (E = 0).  E_c and
+    E_eta (eta = sum_i eta_i) of Eq. error_field are taken at the points of
+    each grid (the reference sampled every finest/n points).  `f32_floor`:
+    the reference case run in FP32 against the FP64 reference, the error
+    FP32 rounding alone leaves after the dynamics amplify it."""
+    import torch
+    from . import fs, inputs as I
+    nmax = max(grids)
+    pre = I.Problem(n=(pre_n, pre_n), dx=(l / pre_n, l / pre_n), p=p)
+    s_pre = periodic_benchmark_state(fs, pre).cpu().numpy()
+
+    def problem(n, dt, lap=0):
+        return I.Problem(n=(n, n), dx=(l / n, l / n), p=p, dt=dt, lap=lap)
+
+    def start(n):
+        return torch.tensor(spectral_resample(s_pre, n), dtype=torch.float64, device="cuda")
+
+    ref_steps = int(round(t_span / ref_dt))
+    f_ref0 = start(nmax)
+    ref, ms_ref = _run(fs, problem(nmax, ref_dt), f_ref0, ref_steps, "f64")
+    refsum = {}
+
+    def errs(n, g):
+        stride = nmax // n
+        if n not in refsum:
+            r = ref[:, ::stride, ::stride]
+            refsum[n] = (r[0], r[1:].sum(0))
+        rc, re = refsum[n]
+        return {"E_c": error_field(rc, g[0]), "E_eta": error_field(re, g[1:].sum(0))}
+
+    g, ms = _run(fs, problem(nmax, ref_dt), f_ref0.float(), ref_steps, "f32")
+    floor = {"grid": nmax, "dt": ref_dt, "steps": ref_steps, "precision": "f32", "ms": ms, **errs(nmax, g)}
+    del f_ref0, g
+    rows = []
+    for n in grids:
+        f0 = start(n) if precision == "f64" else start(n).float()
+        for lap, name in ((0, "FS"), (1, "FSFD2"), (2, "FSFD4")):
+            for dt in dts:
+                steps = int(round(t_span / dt))
+                if n == nmax and lap == 0 and dt == ref_dt and precision == "f64":
+                    g, ms = ref, ms_ref
+                else:
+                    g, ms = _run(fs, problem(n, dt, lap), f0, steps, precision)
+                rows.append({"grid": n, "scheme": name, "precision": precision, "dt": dt, "steps": steps, "ms": ms,
+                             **errs(n, g)})
+        fd_dt = (TABLE1_FD_DT if fd_dts is None else fd_dts).get(n)
+        if fd_dt is not None:
+            steps = int(np.ceil(t_span / fd_dt))
+            if steps <= fd_max_steps:
+                g, ms = _run(fs, problem(n, t_span / steps), start(n), steps, "f64", scheme=fs.FS_SCHEME_EXPLICIT_FD)
+                rows.append({"grid": n, "scheme": "FD", "precision": "f64", "dt": t_span / steps, "steps": steps,
+                             "ms": ms, **errs(n, g)})
+        del f0
+    return {"workload": f"2D {l:g} x {l:g}, p = {p}, benchmark IC at t = 1 (FD on {pre_n}^2), "
+                        f"t = 1 -> {1 + t_span:g}",
+            "reference": {"grid": nmax, "dt": ref_dt, "steps": ref_steps, "precision": "f64", "ms": ms_ref},
+            "f32_floor": floor, "rows": rows}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2306_04322_gb300.experiments")
-    ap.add_argument("study", choices=["precision", "accuracy", "cost"])
+    ap.add_argument("study", choices=["precision", "accuracy", "cost", "table1"])
     ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--t-span", type=float, default=1.0)
     args = ap.parse_args(argv)
     from . import build as B
     B.build()
@@ -168,8 +281,10 @@ def main(argv=None):
         out = precision_study(args.steps or 2000)
     elif args.study == "accuracy":
         out = accuracy_study(args.steps or 10000)
-    else:
+    elif args.study == "cost":
         out = cost_study(args.steps or 200)
+    else:
+        out = table1_study(args.t_span)
     print(json.dumps(out))
 
 

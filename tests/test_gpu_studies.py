@@ -40,3 +40,23 @@ def test_cost_study_small(X):
     assert len(r["rows"]) == 4
     for row in r["rows"]:
         assert row["fs_ms_per_step"] > 0 and row["fd_ms_per_step"] > 0
+
+
+def test_table1_study_small(X):
+    """The Table 1 study on small grids: the reference case is the reference
+    run (E = 0), the time error grows with dt on the finest grid, FP32 stays
+    close to FP64 over a short window, and every case (FS variants, explicit
+    FD) yields finite errors."""
+    from paper_2306_04322_gb300 import inputs as I
+    fd = {n: 0.9 * I.fd_stable_dt(I.Problem(n=(n, n), dx=(200.0 / n,) * 2, p=4)) for n in (32, 64)}
+    r = X.table1_study(t_span=0.05, grids=(32, 64), dts=(2.5e-4, 1e-3, 5e-3), ref_dt=2.5e-4, pre_n=256,
+                       fd_dts=fd)
+    rows = r["rows"]
+    assert len(rows) == 2 * 3 * 3 + 2
+    for row in rows:
+        assert math.isfinite(row["E_c"]) and math.isfinite(row["E_eta"]) and row["E_c"] >= 0
+    fs64 = {row["dt"]: row for row in rows if row["grid"] == 64 and row["scheme"] == "FS"}
+    assert fs64[2.5e-4]["E_c"] == 0.0 and fs64[2.5e-4]["E_eta"] == 0.0
+    assert fs64[1e-3]["E_eta"] < fs64[5e-3]["E_eta"]
+    assert r["f32_floor"]["E_c"] < 1e-9 and r["f32_floor"]["E_eta"] < 1e-9
+    assert {row["scheme"] for row in rows} == {"FS", "FSFD2", "FSFD4", "FD"}
