@@ -341,14 +341,17 @@ __device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T
         // two grid points per pair, lane-wise
         const C c = slot(0, r)[i0];
         C h = vsplat<C>(T(0)), S2 = vsplat<C>(T(0));
-        bad |= !(finite_val(c.x) && finite_val(c.y));
         for (int i = 0; i < p; ++i) {
           const C e = slot(1 + i, r)[i0];
           h = cadd(h, pw.hpoly2(e));
           S2 = vfma(e, e, S2);
-          bad |= !(finite_val(e.x) && finite_val(e.y));
         }
-        slot(nf, r)[i0] = pw.fc2(c, h);
+        // df/dc is non-finite whenever c or any eta_i is: h is a polynomial
+        // in the eta_i and enters with the factor c_beta - c_alpha, and
+        // 0 * inf is NaN, so one test of its two lanes' sum covers all inputs
+        const C fc = pw.fc2(c, h);
+        bad |= !finite_val(fc.x + fc.y);
+        slot(nf, r)[i0] = fc;
         for (int i = 0; i < p; ++i) {
           const C e = slot(1 + i, r)[i0];
           slot(1 + i, r)[i0] = pw.g2(c, e, S2);

@@ -198,6 +198,24 @@ def test_nonfinite_input_reported(F):
     plan.step(2)
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("field,value", [(0, np.inf), (0, np.nan), (1, -np.inf), (2, np.inf), (2, np.nan)])
+def test_nonfinite_in_any_field_reported_by_the_first_step(F, precision, field, value):
+    """One non-finite value in c or in any eta_i is reported by the step that
+    first reads it (p = 2, both precisions)."""
+    import torch
+    pr = I.Problem(n=(64, 32), p=2)
+    pr.dt = 5.0 * I.fd_stable_dt(pr)
+    f0 = I.noise_fields(pr, seed=2)
+    f0[field, 7, 9] = value
+    plan = F.Plan(pr, precision)
+    plan.set_fields(torch.tensor(f0, dtype=torch.float64 if precision == "f64" else torch.float32, device="cuda"))
+    with pytest.raises(F.FSError) as ei:
+        plan.step(1)
+    assert ei.value.status == F.FS_ERR_NONFINITE
+    plan.close()
+
+
 def test_step_before_set_is_a_state_error(F):
     plan = F.Plan(config1(), "f64")
     with pytest.raises(F.FSError) as ei:
