@@ -285,6 +285,15 @@ def roofline_entry(names, alg_bytes, r, peak, peak_kind, traffic_table=None):
                         for n, a, c, m, b in zip(names, avg_ms, r["kern_cnt"], r["kern_ms"], alg_bytes)}}
 
 
+def step_entry(alg_bytes: int, comp_bytes: int, ms: float, peak: float) -> dict:
+    """A whole step against its algorithmic bytes and the compulsory lower
+    bound (state read once and written once)."""
+    gb = lambda b: b / (ms / 1e3) / 1e9
+    return {"ms": ms, "algorithmic_bytes": alg_bytes, "compulsory_bytes": comp_bytes,
+            "algorithmic_GBps": gb(alg_bytes), "compulsory_GBps": gb(comp_bytes),
+            "frac_algorithmic": gb(alg_bytes) / peak, "frac_compulsory": gb(comp_bytes) / peak}
+
+
 def extras(steps: int, warmup: int, device: int, peak, peak_kind):
     """3D 256^3 (p = 2, FP32), 2D 2048^2 (p = 4, FP32) and the 512-member
     ensemble (FP32): throughput and per-pass rooflines, reported beside the
@@ -304,6 +313,7 @@ def extras(steps: int, warmup: int, device: int, peak, peak_kind):
                             "roofline": roofline_entry(["x_pass(fs_row_kernel)", "fs_ypass_kernel<-1>",
                                                         "fs_zstep_kernel", "fs_ypass_kernel<+1>"],
                                                        alg, r, peak, peak_kind, "traffic_3d_256_p2.txt")}
+    out["3d_256_p2_f32"]["roofline"]["step"] = step_entry(sum(alg), 2 * nf * N * s, r["total_ms"] / k, peak)
     # the finest 2D grid of the paper's Table 1 with its five fields (p = 4)
     pr = I.Problem(n=(2048, 2048), p=4)
     pr.dt = 6.0 * I.fd_stable_dt(pr)
@@ -316,6 +326,8 @@ def extras(steps: int, warmup: int, device: int, peak, peak_kind):
                              "roofline": roofline_entry(["fs_row_kernel", "fs_col_kernel"],
                                                         [2 * nf4 * N * s, (2 * nf4 + 1) * N * s], r, peak,
                                                         peak_kind)}
+    out["2d_2048_p4_f32"]["roofline"]["step"] = step_entry((4 * nf4 + 1) * N * s, 2 * nf4 * N * s,
+                                                           r["total_ms"] / k, peak)
     probs = I.batch_problems(512, seed=0)
     kb = max(3, min(steps, 10))
     r = time_plan(probs, "f32", kb, min(warmup, 3), device)
@@ -521,6 +533,9 @@ def main():
             "alg_bytes_per_launch": alg[dom], "avg_launch_ms": avg_ms[dom],
             "kernels": {n: {"avg_ms": a, "launches": c, "share": m / max(sum(r32["kern_ms"]), 1e-30)}
                         for n, a, c, m in zip(names, avg_ms, r32["kern_cnt"], r32["kern_ms"])}}
+    # the whole step against two byte counts: the algorithmic bytes of the two
+    # passes, and the compulsory lower bound (state read once, written once)
+    roof["step"] = step_entry(sum(alg), 2 * nf * npts * s, t32 * 1e3 / args.steps, peak)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t32 * 1e3 / args.steps,

@@ -45,5 +45,7 @@ def test_gpu_arm_line():
     for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
         assert k in roof, k
     assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-9
+    st = roof["step"]
+    assert st["compulsory_bytes"] < st["algorithmic_bytes"] and 0 < st["frac_compulsory"] < st["frac_algorithmic"]
     assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] == 2 * d["steps"]
