@@ -55,6 +55,18 @@ def test_tc_variant_matches_oracle(F, O, precision, n, p):
 
 
 @pytest.mark.parametrize("precision", ["tf32", "bf16x3"])
+def test_tc_variant_2d_several_steps(F, O, precision):
+    """2D steady state (spectra carried from step to step, every forward
+    column transform through the tensor-core stage), ten steps against the
+    oracle."""
+    pr = I.Problem(n=(256, 128), p=2)
+    pr.dt = 6.0 * I.fd_stable_dt(pr)
+    f0 = I.noise_fields(pr, seed=81).astype(np.float32)
+    ref, _ = O.step(pr, f0.astype(np.float64), 10)
+    assert rel_linf(gpu_run(F, pr, f0, 10, precision), ref) <= 10 * TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16x3"])
 def test_tc_variant_256_cube_and_mean(F, O, precision):
     pr = I.Problem(n=(256, 256, 256), p=2)
     pr.dt = 6.0 * I.fd_stable_dt(pr)
