@@ -138,6 +138,11 @@ class ClockSampler:
             for n, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
+        if not os.environ.get("FS_CLOCKS_CSV"):
+            try:
+                os.remove(self.path)  # the temporary sample file
+            except OSError:
+                pass
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
