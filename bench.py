@@ -392,6 +392,25 @@ def _oracle_rate(O, pr, f, seconds: float, min_steps: int = 2):
     return n, time.perf_counter() - t0
 
 
+def cpu_model() -> str:
+    """Host CPU model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_baseline(seconds: float):
     """The oracle (plain FP64 C++ solver) on the host cores, bounded samples of
     whole time steps: the 1024x1024 workload with OpenMP over all cores (the
@@ -406,7 +425,8 @@ def cpu_baseline(seconds: float):
     n, dt = _oracle_rate(O, pr, f, seconds)
     out = {"value": pr.npoints * n / dt, "unit": UNIT, "cores": used, "kind": "oracle",
            "sample": f"{n} whole FP64 oracle time steps of the 1024x1024 p=2 workload "
-                     f"({dt:.1f} s, OpenMP over FFT lines, {used} threads)"}
+                     f"({dt:.1f} s, OpenMP over FFT lines, {used} threads)",
+           "cpu": cpu_model(), "host_cores": cores}
     O.set_threads(1)
     n1, dt1 = _oracle_rate(O, pr, f, seconds / 3, min_steps=1)
     out["single_thread"] = {"value": pr.npoints * n1 / dt1, "unit": UNIT, "cores": 1,
@@ -452,7 +472,8 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("FP32", "FP64 (oracle)"), "grid": list(GRID), "p": P},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model(), "host_cores": cores},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

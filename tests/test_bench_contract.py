@@ -28,6 +28,7 @@ def test_reference_arm_line():
         assert k in d, k
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cpu"] and d["cpu_baseline"]["host_cores"] >= d["cpu_baseline"]["cores"]
 
 
 @pytest.mark.gpu
