@@ -40,6 +40,13 @@ def test_down_then_identity_and_truncation():
 
 
 def test_table1_constants_match_the_paper():
-    assert X.TABLE1_GRIDS == (128, 256, 512, 1024, 2048)
+    """The study's grids and FD time steps against the Table 1 fixture (the
+    2D rows of tests/golden/paper_fd_dt.txt); FS time steps as printed."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_fd_dt.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    fd2 = {int(r[1]): float(r[3]) for r in rows if r[0] == "2"}
+    assert all(float(r[2]) == 200.0 for r in rows if r[0] == "2")
+    assert tuple(sorted(fd2)) == X.TABLE1_GRIDS
+    assert X.TABLE1_FD_DT == fd2
     assert X.TABLE1_FS_DTS == (1e-4, 1e-3, 5e-3)
-    assert X.TABLE1_FD_DT[2048] == 1.490e-7 and X.TABLE1_FD_DT[128] == 8.138e-3
