@@ -144,6 +144,30 @@ def test_free_energy_closed_forms(O):
     assert abs(parts[2]) < 1e-20 and abs(parts[3]) < 1e-20
 
 
+def test_free_energy_closed_forms_3d(O):
+    """The same closed forms on an anisotropic 3D grid (Eq. fe with the 3D
+    frequency vector): uniform fields give f_chem V; one cosine mode in c
+    (eta = 0) gives rho2 V ((cbar - ca)^2 + eps^2 / 2) and kappa_c eps^2 xi^2 V / 4;
+    one cosine mode in eta_1 gives kappa_eta eps^2 xi^2 V / 4 as its gradient part."""
+    pr = I.Problem(n=(8, 16, 4), dx=(1.0, 0.5, 2.0), p=1)
+    V = 8 * 1.0 * 16 * 0.5 * 4 * 2.0
+    f = np.empty((2,) + pr.shape)
+    f[0], f[1] = 0.62, 0.35
+    assert O.free_energy(pr, f) == pytest.approx(O.fchem_point(pr, 0.62, [0.35]) * V, rel=1e-13)
+    eps, cbar = 0.04, 0.55
+    k = (1, 3, 1)
+    xi2 = sum((2 * math.pi * ki / (ni * di)) ** 2 for ki, ni, di in zip(k, pr.n, pr.dx))
+    g = I.cosine_mode_fields(pr, k, cbar, eps, eta_val=0.0)
+    _, parts = O.free_energy(pr, g, parts=True)
+    assert parts[0] == pytest.approx(2.0 * V * ((cbar - 0.3) ** 2 + eps ** 2 / 2), rel=1e-12)
+    assert parts[1] == pytest.approx(3.0 * eps ** 2 * xi2 * V / 4, rel=1e-12)
+    assert abs(parts[2]) < 1e-20
+    h = I.cosine_mode_fields(pr, k, cbar, eps, eta_val=0.5, which=1)
+    _, parts = O.free_energy(pr, h, parts=True)
+    assert abs(parts[1]) < 1e-20
+    assert parts[2] == pytest.approx(3.0 * eps ** 2 * xi2 * V / 4, rel=1e-12)
+
+
 def test_paper_fd_dt_tables_below_von_neumann_bound():
     """Every explicit-FD dt the paper ran (Tables 1 and 2) lies below the
     linearised von Neumann bound used here for 'the FD stable dt'."""
