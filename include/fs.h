@@ -110,8 +110,10 @@ fs_status fs_plan_create_ex(const fs_params* prm, void* stream, fs_alloc_fn allo
 /* Batched ensemble: `count` independent 2D simulations with their own grid
  * sizes and parameters (each[i]), one plan, one launch per pass for all of
  * them.  All members share precision and p; lap and scheme must be
- * spectral FS.  Field pointer arrays for a batch plan are member-major:
- * fields[i * nf + f]. */
+ * spectral FS, precision FS_F64 or FS_F32, 16 <= nx <= 1024 and ny in
+ * [128 (FS_F32) or 64 (FS_F64), 1024]; other members return
+ * FS_ERR_UNSUPPORTED.  Field pointer arrays for a batch plan are
+ * member-major: fields[i * nf + f]. */
 fs_status fs_batch_create(const fs_params* each, int count, void* stream, fs_plan_t* out);
 
 /* Copy the state in: fields[f] points to field f (nf pointers, plan dtype).
@@ -144,7 +146,10 @@ fs_status fs_set_stream(fs_plan_t plan, void* stream);
 /* Total free energy, Eq. (fe), of the current state (rectangle rule, dV =
  * prod dx, gradient terms through Parseval with the plan's |xi|^2).
  * parts (may be NULL) receives 2 + p values: chemical, c-gradient and each
- * eta_i-gradient contribution.  Synchronises. */
+ * eta_i-gradient contribution.  Synchronises.  Built for 2D
+ * semi-implicit FS plans of one simulation; others return
+ * FS_ERR_UNSUPPORTED.  The spectra are overwritten: the next step starts
+ * again from the real fields (as after fs_set_fields). */
 fs_status fs_free_energy(fs_plan_t plan, double* F, double* parts);
 
 /* Adjoint of one step linearised at the state u (nf real field pointers, plan
@@ -152,7 +157,9 @@ fs_status fs_free_energy(fs_plan_t plan, double* F, double* parts);
  * += d<lambda_in, step(u)>/d(M, L, kappa_c, kappa_eta).  The paper has no
  * adjoint; this is the transpose of the Jacobian of the Algorithm-1 step.
  * Uses the plan's workspace (the plan's own state is not modified).
- * Synchronises when grad_theta is not NULL. */
+ * Synchronises when grad_theta is not NULL.  Built for 2D semi-implicit FS
+ * plans of one simulation with axes up to 1024; others return
+ * FS_ERR_UNSUPPORTED. */
 fs_status fs_step_adjoint(fs_plan_t plan, const void* const* u, const void* const* lambda_in,
                           void* const* lambda_out, double grad_theta[4]);
 
