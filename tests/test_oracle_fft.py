@@ -31,7 +31,7 @@ def test_fft_matches_brute_force(O, shape, sign):
     assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("shape", [(64, 64), (8, 32, 16), (1024,), (4, 256)])
+@pytest.mark.parametrize("shape", [(64, 64), (8, 32, 16), (1024,), (4, 256), (2048,), (2, 2048), (2048, 4)])
 def test_fft_matches_numpy(O, shape):
     rng = np.random.default_rng(2)
     a = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
