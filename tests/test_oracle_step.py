@@ -30,7 +30,8 @@ def test_mean_c_conserved(O, n, p):
     assert worst < 1e-13
 
 
-@pytest.mark.parametrize("n,k", [((16, 16), (1, 2)), ((32, 8), (5, 3)), ((8, 8, 8), (1, 2, 3))])
+@pytest.mark.parametrize("n,k", [((16, 16), (1, 2)), ((32, 8), (5, 3)), ((8, 8, 8), (1, 2, 3)),
+                                 ((2048, 4), (37, 1)), ((4, 2048), (1, 611))])
 @pytest.mark.parametrize("lap", [0, 1, 2])
 def test_linear_c_mode_closed_form(O, n, k, lap):
     """eta = 0 is a fixed point (h' = g' = 0) and df/dc = 2 rho^2 (c - c_alpha)
