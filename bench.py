@@ -88,13 +88,18 @@ def dram_traffic(kernel: str, precision: str, table: str = "traffic_2d_1024_p2.t
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    count = 0
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        # the samples go to a temporary file, or to FS_CLOCKS_CSV when set
-        self.path = os.environ.get("FS_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(),
-                                                                     f"fs_clocks_{os.getpid()}_{index}.csv")
+        ClockSampler.count += 1
+        # the samples go to a temporary file of this sampler, or to FS_CLOCKS_CSV
+        # (suffixed by the sampler's number) when set
+        env = os.environ.get("FS_CLOCKS_CSV")
+        self.keep = bool(env)
+        self.path = (f"{env}.{ClockSampler.count}" if env else
+                     os.path.join(tempfile.gettempdir(), f"fs_clocks_{os.getpid()}_{index}_{ClockSampler.count}.csv"))
 
     def __enter__(self):
         try:
@@ -138,7 +143,7 @@ class ClockSampler:
             for n, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
-        if not os.environ.get("FS_CLOCKS_CSV"):
+        if not self.keep:
             try:
                 os.remove(self.path)  # the temporary sample file
             except OSError:
@@ -234,14 +239,49 @@ def time_cufft_structure(steps: int, warmup: int, device: int):
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
     ok = bool(torch.isfinite(u).all())
-    return {"value": pr.npoints / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "finite": ok,
+    # The same step captured once in a CUDA graph and replayed: the library
+    # kernels' own time without the Python dispatch of ~30 eager operations.
+    # The state is copied back into the graph's input outside the timed window.
+    static_u = u.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step(static_u)
+    stream.wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        static_out = step(static_u)
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        flush.zero_()
+        g.replay()
+        static_u.copy_(static_out)
+    torch.cuda.synchronize()
+    gevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        gevs[i][0].record(stream)
+        g.replay()
+        gevs[i][1].record(stream)
+        static_u.copy_(static_out)
+    torch.cuda.synchronize()
+    gms = sum(a.elapsed_time(b) for a, b in gevs) / steps
+    ok = ok and bool(torch.isfinite(static_u).all())
+    del g
+    return {"value": pr.npoints / (gms / 1e3), "unit": UNIT, "ms_per_step": gms, "finite": ok,
+            "eager": {"value": pr.npoints / (ms / 1e3), "unit": UNIT, "ms_per_step": ms},
             "what": "paper's step structure with cuFFT R2C/C2R (torch.fft) and PyTorch elementwise kernels, "
-                    "FP32, same workload; comparison only"}
+                    "FP32, same workload, L2 flushed before every step; the value is one CUDA-graph replay "
+                    "of the whole step (library kernels only), 'eager' the same step launched op by op; "
+                    "comparison only"}
 
 
-def time_plan(probs, precision: str, steps: int, warmup: int, device: int, flush_mb: int = 512):
+def time_plan(probs, precision: str, steps: int, warmup: int, device: int, flush_mb: int = 512, chunk: int = 1):
     """Device time of `steps` steps of a plan (a list of problems = ensemble),
-    L2 flushed before every timed step; per-pass times from the plan."""
+    in calls of fs_step_async(plan, chunk) (chunk >= 32: the captured graph of
+    the time loop), L2 flushed before every timed call; per-pass times from
+    the plan's profiled steps."""
     import torch
     from paper_2306_04322_gb300 import fs, inputs as I
     dtype = torch.float64 if precision == "f64" else torch.float32
@@ -254,18 +294,21 @@ def time_plan(probs, precision: str, steps: int, warmup: int, device: int, flush
     sched = fs.fs_batch_schedule(plan.h) if batch else None
     flush = torch.empty(flush_mb * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{device}")
     stream = torch.cuda.current_stream()
+    calls = max(1, steps // chunk)
     for _ in range(warmup):
         flush.zero_()
-        fs.fs_step_async(plan.h, 1)
+        fs.fs_step_async(plan.h, chunk)
     torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    for i in range(steps):
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(calls)]
+    for i in range(calls):
         flush.zero_()
         evs[i][0].record(stream)
-        fs.fs_step_async(plan.h, 1)
+        fs.fs_step_async(plan.h, chunk)
         evs[i][1].record(stream)
     torch.cuda.synchronize()
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    launches_timed = fs.fs_last_launch_count(plan.h) * calls
+    steps = calls * chunk
     fs.fs_profile_read(plan.h)
     for i in range(steps):
         flush.zero_()
@@ -276,8 +319,8 @@ def time_plan(probs, precision: str, steps: int, warmup: int, device: int, flush
     plan.close()
     del fields, flush
     npts = sum(p.npoints for p in plist)
-    return {"total_ms": total_ms, "kern_ms": kern_ms, "kern_cnt": kern_cnt, "launches": sum(kern_cnt),
-            "workspace_bytes": ws, "npts": npts, "schedule": sched}
+    return {"total_ms": total_ms, "kern_ms": kern_ms, "kern_cnt": kern_cnt, "launches": launches_timed,
+            "workspace_bytes": ws, "npts": npts, "schedule": sched, "steps": steps}
 
 
 def roofline_entry(names, alg_bytes, r, peak, peak_kind, traffic_table=None):
@@ -293,13 +336,65 @@ def roofline_entry(names, alg_bytes, r, peak, peak_kind, traffic_table=None):
                         for n, a, c, m, b in zip(names, avg_ms, r["kern_cnt"], r["kern_ms"], alg_bytes)}}
 
 
-def step_entry(alg_bytes: int, comp_bytes: int, ms: float, peak: float) -> dict:
-    """A whole step against its algorithmic bytes and the compulsory lower
-    bound (state read once and written once)."""
+def step_entry(alg_bytes: int, comp_bytes: int, ms: float, peak: float, design_bytes=None) -> dict:
+    """A whole step against its algorithmic bytes (3 s N per field and pass of
+    the minimal pass structure), the compulsory lower bound (state read once
+    and written once) and, when given, the bytes this design's passes move
+    (fewer than the algorithmic count: c^ carried, one transform of
+    eta - L dt df/deta)."""
     gb = lambda b: b / (ms / 1e3) / 1e9
-    return {"ms": ms, "algorithmic_bytes": alg_bytes, "compulsory_bytes": comp_bytes,
-            "algorithmic_GBps": gb(alg_bytes), "compulsory_GBps": gb(comp_bytes),
-            "frac_algorithmic": gb(alg_bytes) / peak, "frac_compulsory": gb(comp_bytes) / peak}
+    out = {"ms": ms, "algorithmic_bytes": alg_bytes, "compulsory_bytes": comp_bytes,
+           "algorithmic_GBps": gb(alg_bytes), "compulsory_GBps": gb(comp_bytes),
+           "frac_algorithmic": gb(alg_bytes) / peak, "frac_compulsory": gb(comp_bytes) / peak}
+    if design_bytes:
+        out.update({"design_bytes": design_bytes, "frac_design_bytes": gb(design_bytes) / peak})
+    return out
+
+
+def fp64_ops(kernel: str, table: str = "fp64_ops_2d_1024_p2.txt"):
+    """FP64 thread-instructions (DADD + DMUL + DFMA) per launch of a kernel of
+    the 1024^2 p = 2 FP64 step, counted by ncu (committed summary), or None."""
+    path = os.path.join(ROOT, "profiles", table)
+    try:
+        for line in open(path):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == "fp64_ops" and parts[1] == kernel:
+                return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+def fp64_roofline(r64, rate64, hbm_peak, npts: int, nf: int) -> dict:
+    """The FP64 step against min(HBM, FP64 pipe): its floor time is the larger
+    of bytes / HBM bandwidth and FP64 instructions / the measured FP64
+    instruction rate (DADD, DMUL and DFMA each take one FP64 issue slot).
+    Reported for the dominant pass and for the whole step."""
+    names = ["fs_row_kernel", "fs_col_kernel"]
+    dfma, dadd = rate64
+    avg_ms = [m / max(c, 1) for m, c in zip(r64["kern_ms"], r64["kern_cnt"])]
+    dom = max(range(len(avg_ms)), key=lambda i: r64["kern_ms"][i])
+    ops = [fp64_ops(n) for n in names]
+    alg = [3 * nf * npts * 8] * 2
+    step_ms = r64["total_ms"] / max(r64["kern_cnt"][0], 1)
+    out = {"bound": "alu", "kernel": names[dom], "unit": "FP64 Ginst/s", "peak": dfma / 1e9,
+           "peak_source": "measured (project-written DFMA loop, CUDA events, this run)",
+           "peak_dadd": dadd / 1e9, "peak_tflops": 2 * dfma / 1e12, "avg_launch_ms": avg_ms[dom],
+           "hbm": {"achieved": alg[dom] / (avg_ms[dom] / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                   "frac": alg[dom] / (avg_ms[dom] / 1e3) / 1e9 / hbm_peak},
+           "ops_source": "ncu smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum "
+                         "(profiles/fp64_ops_2d_1024_p2.txt)"}
+    if ops[dom] is not None:
+        ach = ops[dom] / (avg_ms[dom] / 1e3) / 1e9
+        out.update({"achieved": ach, "frac": ach / (dfma / 1e9), "ops_per_launch": ops[dom]})
+    else:
+        out.update({"achieved": None, "frac": None, "ops_per_launch": None})
+    if all(o is not None for o in ops):
+        t_alu = sum(ops) / dfma
+        t_hbm = sum(alg) / (hbm_peak * 1e9)
+        out["step"] = {"ms": step_ms, "floor_ms_alu": t_alu * 1e3, "floor_ms_hbm": t_hbm * 1e3,
+                       "frac": max(t_alu, t_hbm) * 1e3 / step_ms}
+    return out
 
 
 def extras(steps: int, warmup: int, device: int, peak, peak_kind):
@@ -313,15 +408,18 @@ def extras(steps: int, warmup: int, device: int, peak, peak_kind):
     k = max(3, min(steps, 20))
     r = time_plan(pr, "f32", k, min(warmup, 3), device)
     nf, s, N = 1 + P, 4, r["npts"]
-    # x 2 nf (c^ carried), y forward 2 nf (c stays in (kx, ky, z) space), z 2 nf + 1, y inverse 2 nf
-    alg = [2 * nf * N * s, 2 * nf * N * s, (2 * nf + 1) * N * s, 2 * nf * N * s]
+    # the algorithmic bytes of the minimal 3D pass structure: 3 s N per field
+    # and pass (12 s N per field and step over the x, y-forward, z and
+    # y-inverse passes)
+    alg = [3 * nf * N * s] * 4
     out["3d_256_p2_f32"] = {"value": N * k / (r["total_ms"] / 1e3), "unit": UNIT, "steps": k,
                             "ms_per_step": r["total_ms"] / k, "dt": pr.dt, "launches": r["launches"],
                             "workspace_bytes": r["workspace_bytes"],
                             "roofline": roofline_entry(["x_pass(fs_row_kernel)", "fs_ypass_kernel<-1>",
                                                         "fs_zstep_kernel", "fs_ypass_kernel<+1>"],
                                                        alg, r, peak, peak_kind, "traffic_3d_256_p2.txt")}
-    out["3d_256_p2_f32"]["roofline"]["step"] = step_entry(sum(alg), 2 * nf * N * s, r["total_ms"] / k, peak)
+    out["3d_256_p2_f32"]["roofline"]["step"] = step_entry(sum(alg), 2 * nf * N * s, r["total_ms"] / k, peak,
+                                                          design_bytes=25 * N * s)
     # the finest 2D grid of the paper's Table 1 with its five fields (p = 4)
     pr = I.Problem(n=(2048, 2048), p=4)
     pr.dt = 6.0 * I.fd_stable_dt(pr)
@@ -332,18 +430,21 @@ def extras(steps: int, warmup: int, device: int, peak, peak_kind):
                              "ms_per_step": r["total_ms"] / k, "dt": pr.dt, "launches": r["launches"],
                              "workspace_bytes": r["workspace_bytes"],
                              "roofline": roofline_entry(["fs_row_kernel", "fs_col_kernel"],
-                                                        [2 * nf4 * N * s, (2 * nf4 + 1) * N * s], r, peak,
-                                                        peak_kind)}
-    out["2d_2048_p4_f32"]["roofline"]["step"] = step_entry((4 * nf4 + 1) * N * s, 2 * nf4 * N * s,
-                                                           r["total_ms"] / k, peak)
+                                                        [3 * nf4 * N * s] * 2, r, peak, peak_kind)}
+    out["2d_2048_p4_f32"]["roofline"]["step"] = step_entry(6 * nf4 * N * s, 2 * nf4 * N * s,
+                                                           r["total_ms"] / k, peak,
+                                                           design_bytes=(4 * nf4 + 1) * N * s)
+    # config 4: the ensemble advanced through its captured graph (32 steps per
+    # graph launch, one persistent launch per pass), two graph calls timed
     probs = I.batch_problems(512, seed=0)
-    kb = max(3, min(steps, 10))
-    r = time_plan(probs, "f32", kb, min(warmup, 3), device)
+    r = time_plan(probs, "f32", 64, 1, device, chunk=32)
+    kb = r["steps"]
     N = r["npts"]
-    alg = [2 * nf * N * s, (2 * nf + 1) * N * s]
+    alg = [3 * nf * N * s] * 2
     out["batched_512_f32"] = {"value": N * kb / (r["total_ms"] / 1e3), "unit": UNIT, "steps": kb,
                               "ms_per_step": r["total_ms"] / kb, "members": 512, "points": N,
-                              "launches": r["launches"], "schedule": {"row_grid": r["schedule"][0],
+                              "launches": r["launches"], "path": "fs_step_async(plan, 32): CUDA-graph replay",
+                              "schedule": {"row_grid": r["schedule"][0],
                                                                        "col_grid": r["schedule"][1],
                                                                        "row_items": r["schedule"][2],
                                                                        "col_items": r["schedule"][3]},
@@ -526,7 +627,9 @@ def main():
     with ClockSampler(torch.cuda.current_device()) as clk:
         r32 = time_gpu("f32", args.steps, args.warmup, local)
     barrier()
-    r64 = time_gpu("f64", args.steps, args.warmup, local)
+    with ClockSampler(torch.cuda.current_device()) as clk64:
+        r64 = time_gpu("f64", args.steps, args.warmup, local)
+        rate64 = fs.fs_measure_fp64_rate()
     barrier()
     e2e = time_e2e(args.steps, args.warmup, local)
     barrier()
@@ -549,10 +652,10 @@ def main():
     s = 4
     nf = 1 + P
     names = ["fs_row_kernel", "fs_col_kernel"]
-    # algorithmic bytes per launch (steady state): the row pass reads the nf
-    # carried half spectra (nf N s bytes: N/2 complex each) and writes nf
-    # (g_i and df/dc); the column pass reads nf + 1 and writes nf.
-    alg = [2 * nf * npts * s, (2 * nf + 1) * npts * s]
+    # algorithmic bytes per launch: the minimal 2D pass structure moves 3 s N
+    # per field in each pass (row: read the half spectrum, write the packed
+    # field and derivative spectra; column: read both, write the update)
+    alg = [3 * nf * npts * s] * 2
     avg_ms = [m / max(c, 1) for m, c in zip(r32["kern_ms"], r32["kern_cnt"])]
     dom = max(range(len(avg_ms)), key=lambda i: r32["kern_ms"][i])
     achieved = alg[dom] / (avg_ms[dom] / 1e3) / 1e9
@@ -562,9 +665,15 @@ def main():
             "alg_bytes_per_launch": alg[dom], "avg_launch_ms": avg_ms[dom],
             "kernels": {n: {"avg_ms": a, "launches": c, "share": m / max(sum(r32["kern_ms"]), 1e-30)}
                         for n, a, c, m in zip(names, avg_ms, r32["kern_cnt"], r32["kern_ms"])}}
-    # the whole step against two byte counts: the algorithmic bytes of the two
-    # passes, and the compulsory lower bound (state read once, written once)
-    roof["step"] = step_entry(sum(alg), 2 * nf * npts * s, t32 * 1e3 / args.steps, peak)
+    # the whole step against the algorithmic bytes of the two passes, the
+    # compulsory lower bound (state read once, written once) and the bytes
+    # this design moves ((4 nf + 1) s N: c^ carried, one transform of g_i)
+    roof["step"] = step_entry(sum(alg), 2 * nf * npts * s, t32 * 1e3 / args.steps, peak,
+                              design_bytes=(4 * nf + 1) * npts * s)
+    fp64 = {"value": job_value(world, npts, args.steps, t64), "unit": UNIT, "ms_per_step": t64 * 1e3 / args.steps,
+            "kernels_ms": r64["kern_ms"], "launches": r64["launches"]}
+    fp64["roofline"] = fp64_roofline(r64, rate64, peak, npts, nf)
+    fp64["clocks"] = clk64.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t32 * 1e3 / args.steps,
@@ -581,8 +690,7 @@ def main():
                        "wall clock"},
         "gpu_launches": r32["launches"],
         "clocks": clk.summary(),
-        "fp64": {"value": job_value(world, npts, args.steps, t64), "unit": UNIT, "ms_per_step": t64 * 1e3 / args.steps,
-                 "kernels_ms": r64["kern_ms"], "launches": r64["launches"]},
+        "fp64": fp64,
         "cufft_structure": cufft,
     }
     line.update(ext)

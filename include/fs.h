@@ -47,6 +47,15 @@
 extern "C" {
 #endif
 
+/* Exported entry points; the library is built with hidden visibility, so
+ * nothing else (C++ templates, function-local statics) is shared with other
+ * libraries loaded in the same process. */
+#if defined(__GNUC__)
+#define FS_API __attribute__((visibility("default")))
+#else
+#define FS_API
+#endif
+
 typedef struct fs_plan* fs_plan_t; /* opaque; owns all device workspace */
 
 typedef enum {
@@ -98,13 +107,16 @@ typedef struct {
 typedef void* (*fs_alloc_fn)(size_t bytes, void* ctx);
 typedef void (*fs_free_fn)(void* ptr, void* ctx);
 
-/* Create a plan for one simulation.  `stream` is a cudaStream_t (NULL: the
+/* Create a plan for one simulation: the initialisation block of Algorithm 1
+ * (parameters of Section 2.1, grid x = [0, l) per axis, dt, and |xi|^2 of
+ * Eq. (Gamma_fft) / (Gamma_fft_3d) or the FS-FD forms, built once as
+ * per-axis tables).  `stream` is a cudaStream_t (NULL: the
  * legacy default stream).  Validates prm first (no CUDA call is made for an
  * invalid request), then allocates the workspace: nf real fields plus
  * (nf + 1) packed half-spectrum slots of N/2 complex values, and small
  * per-axis tables.  On failure *out is NULL. */
-fs_status fs_plan_create(const fs_params* prm, void* stream, fs_plan_t* out);
-fs_status fs_plan_create_ex(const fs_params* prm, void* stream, fs_alloc_fn alloc, fs_free_fn dealloc,
+FS_API fs_status fs_plan_create(const fs_params* prm, void* stream, fs_plan_t* out);
+FS_API fs_status fs_plan_create_ex(const fs_params* prm, void* stream, fs_alloc_fn alloc, fs_free_fn dealloc,
                             void* ctx, fs_plan_t* out);
 
 /* Batched ensemble: `count` independent 2D simulations with their own grid
@@ -114,34 +126,43 @@ fs_status fs_plan_create_ex(const fs_params* prm, void* stream, fs_alloc_fn allo
  * [128 (FS_F32) or 64 (FS_F64), 1024]; other members return
  * FS_ERR_UNSUPPORTED.  Field pointer arrays for a batch plan are
  * member-major: fields[i * nf + f]. */
-fs_status fs_batch_create(const fs_params* each, int count, void* stream, fs_plan_t* out);
+FS_API fs_status fs_batch_create(const fs_params* each, int count, void* stream, fs_plan_t* out);
 
-/* Copy the state in: fields[f] points to field f (nf pointers, plan dtype).
- * Also computes sum(c) in FP64 for the mean-mode carry of FP32 plans. */
-fs_status fs_set_fields(fs_plan_t plan, const void* const* fields);
+/* Copy the state in: the conserved composition c and the order parameters
+ * eta_1 .. eta_p of Section 2.1 (the "initial conditions" input of
+ * Algorithm 1).  fields[f] points to field f (nf pointers, plan dtype).
+ * Also computes sum(c) in FP64 for the mean-mode carry of FP32 plans (the
+ * k = 0 row of Eq. (A-C_discrete_fft_c) is the identity, so mean(c) is
+ * conserved). */
+FS_API fs_status fs_set_fields(fs_plan_t plan, const void* const* fields);
 
 /* Advance nsteps >= 0 time steps (Algorithm 1 iterations, or explicit FD
  * steps for FS_SCHEME_EXPLICIT_FD).  Launches asynchronously, then
  * synchronises the stream and returns FS_ERR_NONFINITE if a non-finite value
  * was met.  Long runs replay a captured CUDA graph of the step. */
-fs_status fs_step(fs_plan_t plan, int64_t nsteps);
+FS_API fs_status fs_step(fs_plan_t plan, int64_t nsteps);
 
-/* As fs_step, without the final synchronisation and status read. */
-fs_status fs_step_async(fs_plan_t plan, int64_t nsteps);
+/* As fs_step -- nsteps iterations of the loop of Algorithm 1 (derivatives,
+ * forward transforms, the per-mode solve of Eqs. (A-C_discrete_fft_c) and
+ * (A-C_discrete_fft_eta), inverse transforms) -- without the final
+ * synchronisation and status read. */
+FS_API fs_status fs_step_async(fs_plan_t plan, int64_t nsteps);
 
 /* Synchronise the plan's stream and return the sticky device status. */
-fs_status fs_sync(fs_plan_t plan);
+FS_API fs_status fs_sync(fs_plan_t plan);
 
-/* Copy the current real fields out (nf pointers).  Materialises them first
- * when the state is held as spectra (one inverse row pass). */
-fs_status fs_get_fields(fs_plan_t plan, void* const* fields_out);
+/* Copy the current real fields c, eta_1 .. eta_p out (nf pointers): the
+ * inverse transforms that close each iteration of Algorithm 1 (its output
+ * step).  Materialises them first when the state is held as spectra (one
+ * inverse row pass); the run continues from the spectra unchanged. */
+FS_API fs_status fs_get_fields(fs_plan_t plan, void* const* fields_out);
 
 /* Replace the physical parameters and dt of an existing plan.  Grid, p,
  * precision, lap and scheme must match the plan; the state is kept. */
-fs_status fs_set_params(fs_plan_t plan, const fs_params* prm);
+FS_API fs_status fs_set_params(fs_plan_t plan, const fs_params* prm);
 
 /* Rebind the plan to another stream. */
-fs_status fs_set_stream(fs_plan_t plan, void* stream);
+FS_API fs_status fs_set_stream(fs_plan_t plan, void* stream);
 
 /* Total free energy, Eq. (fe), of the current state (rectangle rule, dV =
  * prod dx, gradient terms through Parseval with the plan's |xi|^2).
@@ -150,7 +171,7 @@ fs_status fs_set_stream(fs_plan_t plan, void* stream);
  * semi-implicit FS plans of one simulation; others return
  * FS_ERR_UNSUPPORTED.  The spectra are overwritten: the next step starts
  * again from the real fields (as after fs_set_fields). */
-fs_status fs_free_energy(fs_plan_t plan, double* F, double* parts);
+FS_API fs_status fs_free_energy(fs_plan_t plan, double* F, double* parts);
 
 /* Adjoint of one step linearised at the state u (nf real field pointers, plan
  * dtype, device memory): lambda_out = J(u)^T lambda_in, and grad_theta[0..3]
@@ -160,7 +181,7 @@ fs_status fs_free_energy(fs_plan_t plan, double* F, double* parts);
  * Synchronises when grad_theta is not NULL.  Built for 2D semi-implicit FS
  * plans of one simulation with axes up to 1024; others return
  * FS_ERR_UNSUPPORTED. */
-fs_status fs_step_adjoint(fs_plan_t plan, const void* const* u, const void* const* lambda_in,
+FS_API fs_status fs_step_adjoint(fs_plan_t plan, const void* const* u, const void* const* lambda_in,
                           void* const* lambda_out, double grad_theta[4]);
 
 /* Diagnostic timing: as fs_step_async with eager launches (no graph) and a
@@ -169,51 +190,93 @@ fs_status fs_step_adjoint(fs_plan_t plan, const void* const* u, const void* cons
  * count of each pass kind since the last read to ms_per_pass[] and
  * launches_per_pass[] (may be NULL), at most npass_max entries, sets *npass
  * (2D: 0 row pass, 1 column pass) and returns the sticky device status. */
-fs_status fs_step_profiled(fs_plan_t plan, int64_t nsteps);
-fs_status fs_profile_read(fs_plan_t plan, double* ms_per_pass, int64_t* launches_per_pass, int npass_max,
+FS_API fs_status fs_step_profiled(fs_plan_t plan, int64_t nsteps);
+FS_API fs_status fs_profile_read(fs_plan_t plan, double* ms_per_pass, int64_t* launches_per_pass, int npass_max,
                           int* npass);
 
 /* Batched plans: the persistent grid sizes (CTAs) of the row and column
  * launches chosen by the autotuner (it runs inside the first fs_set_fields
  * and times candidate grids on that state), and the work items of each. */
-fs_status fs_batch_schedule(fs_plan_t plan, int64_t* row_grid, int64_t* col_grid, int64_t* row_items,
+FS_API fs_status fs_batch_schedule(fs_plan_t plan, int64_t* row_grid, int64_t* col_grid, int64_t* row_items,
                             int64_t* col_items);
 
-/* Allocation-free 2D step, for callers that cannot allocate device memory
- * (the paper has no counterpart; it is a deployment convenience).  Advances
- * `fields` -- one device array of (1 + p) * nx * ny values in the plan layout
- * (c, eta_1 .. eta_p, x fastest) -- by nsteps semi-implicit FS steps in
- * place, with the same kernels and results as a plan.  All intermediates
- * live in one fixed file-scope device array of 2,228,480 bytes that every GPU
- * loading the library holds until the process exits; the call makes no
- * cudaMalloc / cudaFree and no host heap allocation.
+/* Allocation-free 2D step, for callers that cannot allocate device memory:
+ * a host program whose pool allocator owns all device memory before this
+ * library is loaded, or code on a real-time / signal-handling path where a
+ * cudaMalloc (which can synchronise the device and takes driver locks) is
+ * not allowed.  The paper has no counterpart; it is a deployment
+ * convenience.  Advances `fields` -- one device array of (1 + p) * nx * ny
+ * values in the plan layout (c, eta_1 .. eta_p, x fastest), 16-byte aligned
+ * -- by nsteps semi-implicit FS steps in place, with the same kernels and
+ * results as a plan.  All intermediates live in one fixed file-scope device
+ * array of 2,228,480 bytes that every GPU loading the library holds until
+ * the process exits; the call makes no cudaMalloc / cudaFree and no host
+ * heap allocation.
  *   - Limits: 2D, each axis a power of two in [8, 1024], nx * ny <= 65536,
  *     p <= 2, precision FS_F64 or FS_F32, scheme FS_SCHEME_SEMI_IMPLICIT_FS.
- *     Larger requests return FS_ERR_UNSUPPORTED before any CUDA call; other
- *     bad arguments return FS_ERR_INVALID_ARG.  fs_last_error() is not set.
+ *     Valid requests beyond them (3D, larger grids, p = 3 or 4, the
+ *     tensor-core precisions, the explicit FD scheme) return
+ *     FS_ERR_UNSUPPORTED before any CUDA call.  Malformed arguments (NULL
+ *     pointers, nsteps < 0, a `fields` address that is not 16-byte aligned,
+ *     dt <= 0, p outside [0, 4], unknown enum values) return
+ *     FS_ERR_INVALID_ARG, also before any CUDA call.  fs_last_error() is not
+ *     set.
  *   - The first call on a device looks up the array's device address with
  *     cudaGetSymbolAddress (with that device current); make that first call
  *     before any stream capture.
+ *   - The call copies its tables from a static host array and synchronises
+ *     `stream` (a cudaStream_t) before returning the status, so it returns
+ *     FS_ERR_UNSUPPORTED, enqueueing nothing, when `stream` is capturing.
  *   - Every call shares the array and overwrites it.  Calls whose work
  *     overlaps on the GPU (several streams or host threads at once) race;
- *     serialise them.
- *   - Synchronises `stream` (a cudaStream_t) before returning the status. */
-fs_status fs_step2d_static(const fs_params* prm, void* fields, int64_t nsteps, void* stream);
+ *     serialise them. */
+FS_API fs_status fs_step2d_static(const fs_params* prm, void* fields, int64_t nsteps, void* stream);
+
+/* Kernel forms of the passes (FP32 plans; the paper's method is the same
+ * either way, the rounding order differs).  row_form / col_form: 0 = the
+ * default (the warp-per-line form wherever it applies), 1 = the half-length
+ * row pass / column-tile pass, 2 = the warp-per-line forms: the row pass
+ * transforms two grid rows as one complex line (x lines of 256, 512 or 1024
+ * points), the column pass gives each (column, field) its own warp (2D,
+ * columns of 256, 512 or 1024 points).  Form 2 on a plan it does not
+ * cover returns FS_ERR_UNSUPPORTED; FP64 plans always run form 1.  Used by
+ * the tests (both forms against the oracle) and for A/B timing. */
+FS_API fs_status fs_set_pass_forms(fs_plan_t plan, int row_form, int col_form);
+
+/* Test hook of the failure-detection path (the paper has no counterpart).
+ * With enable != 0, the first bounded device wait of every pass this plan
+ * launches gives up without polling: each pass sets the timeout flag, waits
+ * (bounded) for its own copies to land and returns early, so the next
+ * fs_step / fs_sync returns FS_ERR_TIMEOUT and the fields are unspecified.
+ * enable = 0 restores the normal poll limit; set the fields again before
+ * stepping on.  Nothing hangs or faults: no wait is removed, only the first
+ * one is cut short.  Plans of one simulation only (batched plans return
+ * FS_ERR_UNSUPPORTED). */
+FS_API fs_status fs_test_short_wait(fs_plan_t plan, int enable);
+
+/* Measurement helper (not part of the method): the FP64 instruction rate of
+ * the current device, from a project-written kernel of independent DFMA
+ * chains (and, if dadd_per_s is not NULL, DADD chains) timed with CUDA
+ * events on `stream` (best of three launches after a warm-up).  Rates are
+ * thread-instructions per second; FP64 flop/s = 2 * dfma_per_s.  The FP64
+ * step is bound by this rate, not by HBM.  Allocates and frees 2 KB of
+ * device memory; synchronises the stream. */
+FS_API fs_status fs_measure_fp64_rate(void* stream, double* dfma_per_s, double* dadd_per_s);
 
 /* Device bytes owned by the plan. */
-fs_status fs_workspace_bytes(fs_plan_t plan, size_t* bytes);
+FS_API fs_status fs_workspace_bytes(fs_plan_t plan, size_t* bytes);
 
 /* Number of kernel launches issued by the last fs_step / fs_step_async. */
-fs_status fs_last_launch_count(fs_plan_t plan, int64_t* launches);
+FS_API fs_status fs_last_launch_count(fs_plan_t plan, int64_t* launches);
 
 /* Free everything the plan owns.  NULL is accepted. */
-fs_status fs_destroy(fs_plan_t plan);
+FS_API fs_status fs_destroy(fs_plan_t plan);
 
 /* Text of the last error on `plan` (thread-local text for a NULL plan). */
-const char* fs_last_error(fs_plan_t plan);
+FS_API const char* fs_last_error(fs_plan_t plan);
 
 /* Library version string. */
-const char* fs_version(void);
+FS_API const char* fs_version(void);
 
 #ifdef __cplusplus
 }

@@ -12,6 +12,7 @@ the computation runs in libfs_gb300.so; this module only orders the calls.
 from __future__ import annotations
 
 import torch
+from torch.autograd.function import once_differentiable
 
 from . import fs as _fs
 
@@ -44,7 +45,14 @@ class FSTrajectory(torch.autograd.Function):
         return torch.stack(snaps)
 
     @staticmethod
+    @once_differentiable
     def backward(ctx, gsnap):
+        # The plan (and its device workspace) lives from forward to the one
+        # backward pass that may follow; a second backward through the same
+        # graph (retain_graph=True) would find it closed.
+        if ctx.plan is None:
+            raise RuntimeError("FSTrajectory.backward ran twice on one forward: the plan was released after "
+                               "the first backward; run the forward again")
         plan, every = ctx.plan, ctx.every
         nf = plan.nf
         lam = torch.zeros_like(ctx.checkpoints[0])
@@ -65,6 +73,8 @@ class FSTrajectory(torch.autograd.Function):
                 grad = [a + b for a, b in zip(grad, g)]
                 lam = out
         plan.close()
+        ctx.plan = None
+        ctx.checkpoints = None
         gtheta = torch.tensor(grad, dtype=ctx.theta_dtype, device=ctx.theta_device)
         return gtheta, lam, None, None, None, None
 

@@ -2,6 +2,11 @@
 
 Every translation unit under csrc/ is compiled by nvcc in parallel, then
 linked into one shared library exporting the C ABI of include/fs.h.
+
+build(variant="bounds") builds the bounds-checked library
+_build/bounds/libfs_gb300_bounds.so (FS_DEBUG_BOUNDS: every checked global
+access outside its buffer sets an error bit and is skipped), the substitute
+for a memory checker on small grids; tests load it beside the normal one.
 """
 from __future__ import annotations
 
@@ -18,8 +23,13 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfs_gb300.so")
+VARIANTS = {"release": (BUILD, LIB, []),
+            "bounds": (os.path.join(BUILD, "bounds"), os.path.join(BUILD, "bounds", "libfs_gb300_bounds.so"),
+                       ["-DFS_DEBUG_BOUNDS"])}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# hidden visibility: only the FS_API entry points of include/fs.h are exported
 FLAGS = ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo", "-Xcompiler", "-fPIC",
+         "-Xcompiler", "-fvisibility=hidden", "-Xcompiler", "-fvisibility-inlines-hidden",
          "-I" + INCLUDE, "-I" + CSRC]
 
 
@@ -39,25 +49,26 @@ def _deps():
         [os.path.join(INCLUDE, "fs.h"), os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), variant: str = "release") -> str:
+    out_dir, lib, vflags = VARIANTS[variant]
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     t0 = time.time()
     procs = []
     objs = []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [cc] + ARCH + FLAGS + list(extra_flags) + ["-c", src, "-o", obj]
+        cmd = [cc] + ARCH + FLAGS + vflags + list(extra_flags) + ["-c", src, "-o", obj]
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     errors = []
     for src, pr in procs:
@@ -68,14 +79,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             sys.stdout.write(out.decode(errors="replace"))
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcuda"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print(f"built {LIB} in {time.time() - t0:.1f} s")
-    return LIB
+        print(f"built {lib} in {time.time() - t0:.1f} s")
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
+    build(force="--force" in sys.argv, verbose=True,
+          variant="bounds" if "--bounds" in sys.argv else "release")

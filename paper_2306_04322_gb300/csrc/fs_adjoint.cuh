@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(192) fs_adj_row_fwd_kernel(KArgs a) {
                  bar);
       }
   }
-  if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
+  if (!mbar_wait_bounded(bar, 0, first_wait_polls(a))) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
     mbar_wait_bounded(bar, 0, kWaitPolls);
     return;
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS) fs_adj_col_kernel(KArg
   copy_to_smem(twc, reinterpret_cast<const C*>(a.tw_col), Cfg::TWS);
   for (int i = threadIdx.x; i < NY; i += blockDim.x) k2yt[i] = reinterpret_cast<const T*>(a.k2y)[i];
   __syncthreads();
-  if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
+  if (!mbar_wait_bounded(bar, 0, first_wait_polls(a))) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
     mbar_wait_bounded(bar, 0, kWaitPolls);
     return;
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(192) fs_adj_row_inv_kernel(KArgs a) {
         bulk_g2s(slot(2 * nf + f, r), reinterpret_cast<const C*>(a.aux) + f * half_stride + (row0 + r) * L, bytes,
                  bar);
   }
-  if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
+  if (!mbar_wait_bounded(bar, 0, first_wait_polls(a))) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
     mbar_wait_bounded(bar, 0, kWaitPolls);
     return;

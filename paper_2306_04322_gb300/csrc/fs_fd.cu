@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(FD_TX* FD_TY) fs_fd_kernel(KArgs a, const T* _
   const long long o = (long long)gy * nx + gx;
   const T cn = c + dtM * lmu;
   bool bad = !finite_val(cn);
-  out[o] = cn;
+  const long long out_bytes = (long long)nf * N * (long long)sizeof(T);
+  if (in_bounds(a, &out[o], sizeof(T), out, out_bytes)) out[o] = cn;
   T S2 = T(0);
   for (int f = 1; f < nf; ++f) {
     const T e = at(f, ly, lx);
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(FD_TX* FD_TY) fs_fd_kernel(KArgs a, const T* _
     const T e = at(f, ly, lx);
     const T en = e - dtL * (pw.feta(c, e, S2) - ke * lap(f, ly, lx));
     bad |= !finite_val(en);
-    out[f * N + o] = en;
+    if (in_bounds(a, &out[f * N + o], sizeof(T), out, out_bytes)) out[f * N + o] = en;
   }
   if (bad) atomicOr(a.flag, FS_FLAG_NONFINITE);
 }

@@ -275,6 +275,34 @@ __device__ __forceinline__ void line_fft(C (&v)[E], int t, const C* __restrict__
   stockham<L, E, 1, DIR>(v, t, twp, st, ld, sync);
 }
 
+// Line FFT of length L = E * E held by one warp-sized group of E threads
+// with E values each (E = 32: 1024 points, one warp): two radix-E passes and
+// one exchange, as line_fft, but both passes run the same loop body, so the
+// radix-E butterfly code is emitted once (half the instruction footprint of
+// the unrolled pass sequence; the instruction cache is what the warp-per-line
+// kernels run short of).  twp: the pass table of (L, E), entries [r][j] of
+// the second pass (sub-length E).
+template <int E, int DIR, typename C, class Store, class Load, class Sync>
+__device__ __forceinline__ void line_fft_sq(C (&v)[E], int t, const C* __restrict__ twp, Store st, Load ld,
+                                            Sync sync) {
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+#pragma unroll
+      for (int r = 1; r < E; ++r) v[r] = mul_tw<DIR>(v[r], twp[r * E + t]);
+    }
+    reg_dft<E, DIR, 1>(v);
+    if (pass == 0) {
+      sync();
+#pragma unroll
+      for (int r = 0; r < E; ++r) st(t * E + r, v[r]);
+      sync();
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = ld(t + E * m);
+    }
+  }
+}
+
 // Padded shared-memory indices: one spare slot every 32 (pad32) or 16
 // (pad16) elements.  pad16 keeps the radix-16 butterfly writes (16
 // consecutive elements per thread) and the stride-TPL reads of the row
@@ -357,6 +385,32 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0,
       "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
+// Named CTA barriers (PTX bar.sync / bar.arrive with an id and a thread
+// count, a multiple of 32): bar_sync waits until `count` threads have
+// arrived at barrier `id`; bar_arrive counts this warp in without waiting
+// (producer side).  Shared-memory writes before the arrive are visible to
+// the threads that pass the matching bar_sync.  Id 0 is __syncthreads().
+__device__ __forceinline__ void bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// 3D tiled TMA store shared -> global (bulk-group completion); the innermost
+// coordinate times the element size must be a multiple of 16 bytes and no
+// coordinate may be negative.  The writing threads order their generic
+// shared-memory stores before it with fence_proxy_async_smem() and a barrier.
+__device__ __forceinline__ void tma_store_3d(const void* tmap, int c0, int c1, int c2, const void* src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(tmap),
+               "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Waits until every committed bulk group of this thread has completed (its
+// global writes performed).
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // Bounded wait: true when the phase completed, false after `limit` polls.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
   for (uint32_t i = 0; i < limit; ++i)

@@ -37,6 +37,8 @@ struct KArgs {
   const void* tw_z;        // pass tables of the z line FFT (L = nz, 3D)
   const void* tw_row_w;    // pass tables of the x line FFT with 32 values per thread (FP32, nx = 1024; NULL: none)
   const void* tw_half;     // exp(-2 pi i k / nx), k = 0..nx/2-1 (real <-> half-length complex)
+  const void* tw_row2;     // pass tables of the x line FFT of the pair form (L = nx, E = nx / 32; NULL: none)
+  const void* tw_col2;     // pass tables of the y line FFT of the warp-per-column form (L = ny, E = ny / 32)
   const void* tc_b;        // tensor-core DFT stage: split 16-point DFT matrix, [hi | lo][32][32] float
   const void* k2x;         // |xi_x|^2 per x bin, nx/2 + 1 entries
   const void* k2y;         // |xi_y|^2 per y bin, ny entries
@@ -56,6 +58,11 @@ struct KArgs {
   const double* csum;      // FP64 sum of c carried for the k = 0 mode (NULL: off)
   double* acc;             // FP64 accumulators of the free-energy diagnostic (2 + p)
   int* flag;               // sticky error bits (FS_FLAG_*)
+  int short_wait;          // test hook: nonzero makes the first bounded wait of every pass give up
+                           // without polling (the pass reports FS_FLAG_TIMEOUT; the kernels still
+                           // wait, bounded, for their own copies before exiting); 0 = normal
+  long long spec_bytes;    // bytes of the buffer `spec` points into (index checks of FS_DEBUG_BOUNDS builds)
+  long long real_bytes;    // bytes of the buffer `real` points into (same)
   Coef<float> cf;          // coefficients, FP32 copy
   Coef<double> cd;         // coefficients, FP64 copy
 };
@@ -70,6 +77,15 @@ cudaError_t row_launch_f32(const KArgs& a, cudaStream_t s);
 cudaError_t row_launch_f64(const KArgs& a, cudaStream_t s);
 cudaError_t col_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
 cudaError_t col_launch_f64(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
+// Warp-per-line forms (FP32; fs_k2d_v2.cuh): the row pass in pair form for
+// nx in {256, 512, 1024} (modes 0, 1, 2; needs KArgs::tw_row2) and the column
+// pass with one warp per (column, slot) for ny in {256, 512, 1024} (needs
+// KArgs::tw_col2 and a tensor map with 2-column boxes).  Return
+// cudaErrorNotSupported for other requests.
+cudaError_t row2_launch_f32(const KArgs& a, cudaStream_t s);
+cudaError_t col2_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
+bool row2_supported(int nx, int nf);
+bool col2_supported(int ny, int nf);
 // Free-energy diagnostic, 2D (row pass mode 3 does the chemical sum and the
 // x transforms): y transforms and sums of w K2 |phi^|^2 per field.
 cudaError_t energy_col_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(LineCfg<T, NY>::THREADS, 4)
   }
   copy_to_smem(tw, reinterpret_cast<const C*>(a.tw_col), Cfg::TWS);
   __syncthreads();
-  if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
+  if (!mbar_wait_bounded(bar, 0, first_wait_polls(a))) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
     mbar_wait_bounded(bar, 0, kWaitPolls);
     return;
@@ -166,7 +166,8 @@ __global__ void __launch_bounds__(LineCfg<T, NY>::THREADS, 4)
   }
   C* S = reinterpret_cast<C*>(a.spec) + (long long)oplane * NY * Lh + kx0 + j;
 #pragma unroll
-  for (int m = 0; m < E; ++m) S[(long long)(t + TPL * m) * Lh] = v[m];
+  for (int m = 0; m < E; ++m)
+    if (spec_ok(a, &S[(long long)(t + TPL * m) * Lh], sizeof(C))) S[(long long)(t + TPL * m) * Lh] = v[m];
 }
 
 // ---------------------------------------------------------------------------
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(LineCfg<T, NZ>::THREADS, 4)
   copy_to_smem(tw, reinterpret_cast<const C*>(a.tw_z), Cfg::TWS);
   for (int i = threadIdx.x; i < NZ; i += blockDim.x) k2zt[i] = reinterpret_cast<const T*>(a.k2z)[i];
   __syncthreads();
-  if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
+  if (!mbar_wait_bounded(bar, 0, first_wait_polls(a))) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
     mbar_wait_bounded(bar, 0, kWaitPolls);
     return;
@@ -306,7 +307,8 @@ __global__ void __launch_bounds__(LineCfg<T, NZ>::THREADS, 4)
   }
   C* S = reinterpret_cast<C*>(a.spec) + (long long)(g == 0 ? 0 : g) * a.slot_stride + (long long)ky * Lh + kx;
 #pragma unroll
-  for (int m = 0; m < E; ++m) S[(long long)(t + TPL * m) * zstride] = v[m];
+  for (int m = 0; m < E; ++m)
+    if (spec_ok(a, &S[(long long)(t + TPL * m) * zstride], sizeof(C))) S[(long long)(t + TPL * m) * zstride] = v[m];
 }
 
 // ---- launchers ---------------------------------------------------------------

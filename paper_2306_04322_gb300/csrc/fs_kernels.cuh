@@ -90,6 +90,33 @@ struct Pointwise {
   }
 };
 
+// Polls of the first bounded wait of a pass: kWaitPolls, or none when the
+// plan's test hook asks every pass to report a timeout.  The wait that
+// follows a timeout (letting the CTA's own copies land) keeps kWaitPolls.
+__device__ __forceinline__ uint32_t first_wait_polls(const KArgs& a) { return a.short_wait ? 0u : kWaitPolls; }
+
+// Index checks of the bounds-checked build (compiled with FS_DEBUG_BOUNDS):
+// an access of `bytes` at p outside [base, base + extent) sets
+// FS_FLAG_BOUNDS and is skipped instead of reaching memory.  In the normal
+// build this is `true` and costs nothing.
+__device__ __forceinline__ bool in_bounds(const KArgs& a, const void* p, long long bytes, const void* base,
+                                          long long extent) {
+#ifdef FS_DEBUG_BOUNDS
+  const long long off = (long long)((const char*)p - (const char*)base);
+  if (off < 0 || off + bytes > extent) {
+    atomicOr(a.flag, FS_FLAG_BOUNDS);
+    return false;
+  }
+#endif
+  return true;
+}
+__device__ __forceinline__ bool spec_ok(const KArgs& a, const void* p, long long bytes) {
+  return in_bounds(a, p, bytes, a.spec, a.spec_bytes);
+}
+__device__ __forceinline__ bool real_ok(const KArgs& a, const void* p, long long bytes) {
+  return in_bounds(a, p, bytes, a.real, a.real_bytes);
+}
+
 template <typename T>
 __device__ __forceinline__ bool finite_val(T x) {
   return isfinite(x);
@@ -175,7 +202,12 @@ __device__ __forceinline__ void row_issue(const KArgs& a, long long rb, cplx<T>*
     // 3D carry: c's x spectrum sits in slot nf (see the 3D passes)
     const int sl = (f == 0 && a.carry3) ? nf : f;
     const C* src = from_real ? realc + f * (a.npts / 2) + row0 * L : spec + sl * a.slot_stride + row0 * L;
-    for (int r = 0; r < Reff; ++r) bulk_g2s(in + (f * R + r) * PL, src + r * L, bytes, bar);
+    for (int r = 0; r < Reff; ++r) {
+      // a skipped copy leaves the barrier short of bytes: the pass then
+      // reports a timeout besides the index error
+      if (from_real ? real_ok(a, src + r * L, bytes) : spec_ok(a, src + r * L, bytes))
+        bulk_g2s(in + (f * R + r) * PL, src + r * L, bytes, bar);
+    }
   }
 }
 
@@ -259,7 +291,8 @@ __device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T
           C* dst = realc + f * half_stride + row * L;
           if (active) {
 #pragma unroll
-            for (int m = 0; m < E; ++m) dst[t + TPL * m] = cconj(v[m]);
+            for (int m = 0; m < E; ++m)
+              if (real_ok(a, &dst[t + TPL * m], sizeof(C))) dst[t + TPL * m] = cconj(v[m]);
           }
         } else {
           wsync();
@@ -291,7 +324,7 @@ __device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T
             // mode 1, c: store in the carried scaling, x spectrum / nx (what
             // the column pass leaves behind), 2 x^ / (2 nx) (exact: power of 2)
             if (c_carried) out = cscale(out, c_scale);
-            P[k] = out;
+            if (spec_ok(a, &P[k], sizeof(C))) P[k] = out;
           }
         }
       }
@@ -385,7 +418,7 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
     row_issue<T, NX, W>(a, rb, slots, bar);
   }
   griddep_launch_dependents();
-  if (!mbar_wait_bounded(bar, parity, kWaitPolls)) {
+  if (!mbar_wait_bounded(bar, parity, first_wait_polls(a))) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
     mbar_wait_bounded(bar, parity, kWaitPolls);  // let the copies land before exiting
     return false;
@@ -514,7 +547,7 @@ __device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap
   griddep_wait();
   griddep_launch_dependents();
   __syncthreads();
-  if (!mbar_wait_bounded(bar, parity, kWaitPolls)) {
+  if (!mbar_wait_bounded(bar, parity, first_wait_polls(a))) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
     mbar_wait_bounded(bar, parity, kWaitPolls);
     return false;
@@ -617,7 +650,8 @@ __device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap
   }
   C* S = reinterpret_cast<C*>(a.spec) + kx + (long long)(g == 0 ? 0 : g) * a.slot_stride;
 #pragma unroll
-  for (int m = 0; m < E; ++m) S[(long long)(t + TPL * m) * Lh] = cconj(v[m]);
+  for (int m = 0; m < E; ++m)
+    if (spec_ok(a, &S[(long long)(t + TPL * m) * Lh], sizeof(C))) S[(long long)(t + TPL * m) * Lh] = cconj(v[m]);
   return true;
 }
 
@@ -653,7 +687,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, 2)
   copy_to_smem(twc, reinterpret_cast<const C*>(a.tw_col), Cfg::TWS);
   for (int i = threadIdx.x; i < NY; i += blockDim.x) k2yt[i] = reinterpret_cast<const T*>(a.k2y)[i];
   __syncthreads();
-  if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
+  if (!mbar_wait_bounded(bar, 0, first_wait_polls(a))) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
     mbar_wait_bounded(bar, 0, kWaitPolls);
     return;

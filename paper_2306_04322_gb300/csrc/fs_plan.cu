@@ -39,10 +39,13 @@ struct Member {
   void* tw_half = nullptr;
   void* tw_row_w = nullptr;  // x-pass tables with 32 values per thread (FP32 rows of 1024)
   void* tc_b = nullptr;  // split DFT matrix of the tensor-core stage (TC precisions)
+  void* tw_row2 = nullptr;  // x-line tables of the pair-form row pass (FP32, nx in {256, 512, 1024})
+  void* tw_col2 = nullptr;  // y-line tables of the warp-per-column pass (FP32 2D, ny in {256, 512, 1024})
   double* csum = nullptr;
   long long slot_stride = 0;
   CUtensorMap tmap_col;  // [slot * nz + z][y][kx] tiles of the 2D column pass / 3D y passes
   CUtensorMap tmap_z;    // [slot][z][y][kx] z lines of the 3D z step
+  CUtensorMap tmap_col2; // [slot][y][kx] two-column tiles of the warp-per-column pass
   int fd_cur = 0;        // explicit FD: 0 state in `real`, 1 state in `spec` (as real fields)
   // adjoint workspace (allocated on first use)
   void* aspec = nullptr;  // 3 nf packed half-spectrum slots
@@ -77,6 +80,9 @@ struct fs_plan {
   cudaGraphExec_t gexec = nullptr;
   int gsteps = 0;
   int64_t last_launches = 0;
+  int short_wait = 0;  // test hook of fs_test_short_wait
+  int row_form = 0;    // fs_set_pass_forms: 0 default, 1 half-length / tile kernels, 2 warp-per-line kernels
+  int col_form = 0;
   std::vector<cudaEvent_t> ev_pool;  // fs_step_profiled timing events
   std::vector<int> ev_kind;
   size_t ev_used = 0;
@@ -243,6 +249,8 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   a.tw_z = m.tw_z;
   a.tw_half = m.tw_half;
   a.tw_row_w = m.tw_row_w;
+  a.tw_row2 = (p->row_form == 1) ? nullptr : m.tw_row2;
+  a.tw_col2 = (p->col_form == 1) ? nullptr : m.tw_col2;
   a.tc_b = m.tc_b;
   a.k2x = m.k2x;
   a.k2y = m.k2y;
@@ -273,15 +281,29 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   a.csum = p->f64 ? nullptr : m.csum;
   a.flag = p->flag;
   a.acc = p->acc;
+  a.short_wait = p->short_wait;
+  const long long rs = p->f64 ? 8 : 4;
+  a.spec_bytes = (long long)(p->nf + 1) * m.slot_stride * 2 * rs;
+  a.real_bytes = (long long)p->nf * m.npts * rs;
   fill_coef(a.cd, m.prm, a.scale);
   fill_coef(a.cf, m.prm, a.scale);
   return a;
 }
 
+// FP32 plans take the warp-per-line forms where they apply (KArgs::tw_row2 /
+// tw_col2 set), else the half-length row / tile column kernels.
 cudaError_t launch_row(const fs_plan* p, const fs::KArgs& a, cudaStream_t s) {
+  if (!p->f64 && a.tw_row2) {
+    cudaError_t e = fs::row2_launch_f32(a, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   return p->f64 ? fs::row_launch_f64(a, s) : fs::row_launch_f32(a, s);
 }
 cudaError_t launch_col(const fs_plan* p, const Member& m, const fs::KArgs& a, cudaStream_t s) {
+  if (!p->f64 && a.tw_col2) {
+    cudaError_t e = fs::col2_launch_f32(a, m.tmap_col2, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   return p->f64 ? fs::col_launch_f64(a, m.tmap_col, s) : fs::col_launch_f32(a, m.tmap_col, s);
 }
 
@@ -304,6 +326,18 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
+// Where the warp-per-line forms apply: FP32 (plain, and the row pass also
+// for the tensor-core precisions, whose stage is in the column transforms),
+// semi-implicit FS; rows of 256, 512 or 1024 points (2D rows and 3D x
+// lines); 2D columns of 256, 512 or 1024 points with no tensor-core stage.
+bool row2_form(const fs_params& prm, bool f64) {
+  return !f64 && prm.scheme == FS_SCHEME_SEMI_IMPLICIT_FS && fs::row2_supported(prm.n[0], 1 + prm.p);
+}
+bool col2_form(const fs_params& prm, bool f64) {
+  return !f64 && prm.scheme == FS_SCHEME_SEMI_IMPLICIT_FS && prm.ndim == 2 && prm.precision == FS_F32 &&
+         fs::col2_supported(prm.n[1], 1 + prm.p);
+}
+
 // Tensor map over the spectrum slots viewed as [nf + 1][ny][W] 8-byte units
 // (W = nx/2 for FP32 complex, nx for FP64 complex); box = one column tile of
 // the column pass, up to 256 rows.
@@ -322,6 +356,17 @@ bool encode_col_map(Member& m, int nslots, bool f64) {
     cuuint32_t box[3] = {(cuuint32_t)(tk * units), (cuuint32_t)(ny < 256 ? ny : 256), 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(&m.tmap_col, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, m.spec, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+  }
+  if (col2_form(m.prm, f64)) {
+    // [slot][y][kx]: two-column tiles (16-byte rows) of the warp-per-column pass
+    cuuint64_t dims[3] = {W, (cuuint64_t)ny, (cuuint64_t)nslots};
+    cuuint64_t strides[2] = {W * 8, W * 8 * ny};
+    cuuint32_t box[3] = {2, (cuuint32_t)(ny < 256 ? ny : 256), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&m.tmap_col2, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, m.spec, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return false;
@@ -465,7 +510,7 @@ fs_status read_flag(fs_plan* p) {
 //   tw_half[nx/2]                           (exp(-2 pi i k / nx), complex)
 //   tc_b[2048] (TC precisions only)         (split DFT matrix of the tensor-core stage, 32-bit words)
 struct TableLayout {
-  size_t k2x, k2y, k2z, tw_row, tw_row_w, tw_col, tw_z, tw_half, tc_b, total;  // offsets in bytes
+  size_t k2x, k2y, k2z, tw_row, tw_row_w, tw_col, tw_z, tw_half, tc_b, tw_row2, tw_col2, total;  // offsets (bytes)
   int Lrow, Erow, Lcol, Ecol, Lz, Ez;
 };
 
@@ -577,6 +622,10 @@ TableLayout table_layout(const fs_params& prm, bool f64) {
   o = align16(o + cs * (nx / 2));
   t.tc_b = o;
   o = align16(o + (tc_split(prm.precision) ? 2048 * sizeof(float) : 0));
+  t.tw_row2 = o;  // pair-form row pass: L = nx, E = nx / 32
+  o = align16(o + (row2_form(prm, f64) ? cs * fs::pass_table_size(nx, nx / 32) : 0));
+  t.tw_col2 = o;  // warp-per-column pass: L = ny, E = ny / 32
+  o = align16(o + (col2_form(prm, f64) ? cs * fs::pass_table_size(ny, ny / 32) : 0));
   t.total = o;
   return t;
 }
@@ -626,7 +675,9 @@ cudaError_t upload_tables(Member& m, bool f64, char* dev, size_t bytes) {
   for (int k = 0; k <= nx / 2; ++k) kx[k] = axis_k2(prm.lap, k, nx, prm.dx[0]);
   for (int k = 0; k < ny; ++k) ky[k] = axis_k2(prm.lap, k, ny, prm.dx[1]);
   for (int k = 0; k < nz && prm.ndim > 2; ++k) kz[k] = axis_k2(prm.lap, k, nz, prm.dx[2]);
-  std::vector<long double> rr, ii, wr, wi, cr, ci, zr, zi, hr, hi;
+  std::vector<long double> rr, ii, wr, wi, cr, ci, zr, zi, hr, hi, r2r, r2i, c2r, c2i;
+  if (row2_form(prm, f64)) pass_table(nx, nx / 32, r2r, r2i);
+  if (col2_form(prm, f64)) pass_table(ny, ny / 32, c2r, c2i);
   pass_table(t.Lrow, t.Erow, rr, ii);
   if (wide_rows(prm, f64)) pass_table(t.Lrow, 32, wr, wi);
   pass_table(t.Lcol, t.Ecol, cr, ci);
@@ -654,6 +705,8 @@ cudaError_t upload_tables(Member& m, bool f64, char* dev, size_t bytes) {
     put_cplx<float>(buf, t.tw_col, cr, ci);
     put_cplx<float>(buf, t.tw_z, zr, zi);
     put_cplx<float>(buf, t.tw_half, hr, hi);
+    put_cplx<float>(buf, t.tw_row2, r2r, r2i);
+    put_cplx<float>(buf, t.tw_col2, c2r, c2i);
   }
   m.k2x = dev + t.k2x;
   m.k2y = dev + t.k2y;
@@ -663,6 +716,8 @@ cudaError_t upload_tables(Member& m, bool f64, char* dev, size_t bytes) {
   m.tw_col = dev + t.tw_col;
   m.tw_z = dev + t.tw_z;
   m.tw_half = dev + t.tw_half;
+  m.tw_row2 = row2_form(prm, f64) ? dev + t.tw_row2 : nullptr;
+  m.tw_col2 = col2_form(prm, f64) ? dev + t.tw_col2 : nullptr;
   if (const int mode = tc_split(prm.precision)) {
     tc_table(mode, reinterpret_cast<uint32_t*>(buf.data() + t.tc_b));
     m.tc_b = dev + t.tc_b;
@@ -1115,6 +1170,8 @@ fs_status fs_step_adjoint(fs_plan_t p, const void* const* u, const void* const* 
   a.spec = m.aspec;
   a.slot_stride = m.slot_stride;
   a.real = m.alam;
+  a.spec_bytes = (long long)3 * nf * m.slot_stride * (long long)cs;
+  a.real_bytes = (long long)nf * m.npts * (long long)rs;
   a.aux = m.au;
   if (e == cudaSuccess)
     e = p->f64 ? fs::adjoint_launch_f64(a, m.tmap_adj, m.aout, p->stream)
@@ -1222,6 +1279,27 @@ fs_status fs_profile_read(fs_plan_t p, double* ms_per_pass, int64_t* launches_pe
   }
   *npass = n;
   return read_flag(p);
+}
+
+fs_status fs_set_pass_forms(fs_plan_t p, int row_form, int col_form) {
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  if (row_form < 0 || row_form > 2 || col_form < 0 || col_form > 2)
+    return fail(p, FS_ERR_INVALID_ARG, "pass forms are 0 (default), 1 (half-length / tile) or 2 (warp per line)");
+  const Member& m = p->members[0];
+  if ((row_form == 2 && !m.tw_row2) || (col_form == 2 && !m.tw_col2))
+    return fail(p, FS_ERR_UNSUPPORTED, "the warp-per-line form does not cover this plan's grid or precision");
+  p->row_form = row_form;
+  p->col_form = col_form;
+  drop_graph(p);  // the captured launches hold the arguments by value
+  return FS_OK;
+}
+
+fs_status fs_test_short_wait(fs_plan_t p, int enable) {
+  if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
+  if (p->batch) return fail(p, FS_ERR_UNSUPPORTED, "fs_test_short_wait is built for plans of one simulation");
+  p->short_wait = enable ? 1 : 0;
+  drop_graph(p);  // the captured launches hold the arguments by value
+  return FS_OK;
 }
 
 fs_status fs_batch_schedule(fs_plan_t p, int64_t* row_grid, int64_t* col_grid, int64_t* row_items,

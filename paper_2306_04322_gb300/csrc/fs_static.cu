@@ -1,12 +1,13 @@
 // fs_step2d_static: the 2D semi-implicit Fourier-spectral step for callers
-// that cannot allocate device memory -- for example code running where
-// cudaMalloc is not allowed (inside a CUDA stream capture that must not
-// allocate, an embedding that owns all device memory through its own
-// allocator, or a signal-safe / real-time context).  It runs the same row and
-// column kernels as a plan, but every intermediate (the packed spectra, the
-// twiddle and |xi|^2 tables, the status flag and the FP64 mean carry) lives
-// in one file-scope device array of fixed size, so the call allocates
-// nothing: no cudaMalloc, no cudaFree, no host heap.
+// that cannot allocate device memory -- for example a host application that
+// hands every byte of device memory to its own pool allocator before loading
+// this library, or code on a real-time or signal-handling path where a
+// cudaMalloc (which may synchronise the device and take driver locks) is not
+// allowed.  It runs the same row and column kernels as a plan, but every
+// intermediate (the packed spectra, the twiddle and |xi|^2 tables, the
+// status flag and the FP64 mean carry) lives in one file-scope device array
+// of fixed size, so the call allocates nothing: no cudaMalloc, no cudaFree,
+// no host heap.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -101,8 +102,20 @@ void fill_coef_static(fs::Coef<T>& k, const fs_params& q, double scale) {
   k.dt = (T)q.dt;
 }
 
-// Builds the tables in g_host_tables; returns their byte size and the
-// offsets of each table (relative to the table region).
+// Byte size of the tables build_tables writes for grid (nx, ny).
+template <typename T>
+size_t tables_bytes(int nx, int ny) {
+  const bool f64 = sizeof(T) == 8;
+  size_t o = up16(sizeof(T) * (nx / 2 + 1));
+  o = up16(o + sizeof(T) * ny);
+  o = up16(o + 2 * sizeof(T) * (size_t)fs::pass_table_size(nx / 2, fs::row_E(nx / 2, f64)));
+  o = up16(o + 2 * sizeof(T) * (size_t)fs::pass_table_size(ny, fs::col_E(ny, f64)));
+  return up16(o + 2 * sizeof(T) * (nx / 2));
+}
+
+// Builds the tables in g_host_tables (the caller has checked that they fit:
+// tables_bytes <= kTableBytes); returns their byte size and the offsets of
+// each table (relative to the table region).
 template <typename T>
 size_t build_tables(const fs_params& q, size_t off[5]) {
   const int nx = q.n[0], ny = q.n[1];
@@ -143,6 +156,7 @@ fs_status run_static(const fs_params& q, void* fields, int64_t nsteps, cudaStrea
   const int nx = q.n[0], ny = q.n[1], nf = 1 + q.p;
   const long long N = (long long)nx * ny;
   size_t off[5];
+  if (tables_bytes<T>(nx, ny) > kTableBytes) return FS_ERR_UNSUPPORTED;
   const size_t tbytes = build_tables<T>(q, off);
   unsigned char* tables = scratch + kHeadBytes;
   unsigned char* spec = scratch + kSpecOffset;
@@ -179,6 +193,8 @@ fs_status run_static(const fs_params& q, void* fields, int64_t nsteps, cudaStrea
   a.scale = 1.0 / (2.0 * (double)N);
   a.inv_npts = 1.0 / (double)N;
   a.flag = reinterpret_cast<int*>(scratch);
+  a.spec_bytes = (long long)(nf + 1) * (N / 2) * 2 * (long long)sizeof(T);
+  a.real_bytes = (long long)nf * N * (long long)sizeof(T);
   a.csum = f64 ? nullptr : reinterpret_cast<double*>(scratch + 8);
   a.acc = reinterpret_cast<double*>(scratch + 64);
   fill_coef_static(a.cd, q, a.scale);
@@ -226,15 +242,30 @@ fs_status run_static(const fs_params& q, void* fields, int64_t nsteps, cudaStrea
 }  // namespace
 
 extern "C" fs_status fs_step2d_static(const fs_params* prm, void* fields, int64_t nsteps, void* stream) {
-  if (!prm || !fields || nsteps < 0) return FS_ERR_INVALID_ARG;
+  // Malformed arguments: FS_ERR_INVALID_ARG.  The kernels read and write the
+  // fields with 16-byte bulk copies and vector stores, so the array must
+  // start on a 16-byte boundary (a tensor view with an odd storage offset
+  // does not); rejecting it here keeps a misaligned access off the GPU.
+  if (!prm || !fields || nsteps < 0 || ((uintptr_t)fields & 15) != 0) return FS_ERR_INVALID_ARG;
   const fs_params& q = *prm;
-  if (q.ndim != 2 || q.p < 0 || q.p > 4 || !(q.dt > 0.0) || !std::isfinite(q.dt) || !(q.dx[0] > 0.0) ||
-      !(q.dx[1] > 0.0) || (q.precision != FS_F64 && q.precision != FS_F32) || q.lap < 0 || q.lap > 2 ||
-      q.scheme != FS_SCHEME_SEMI_IMPLICIT_FS)
+  if ((q.ndim != 2 && q.ndim != 3) || q.p < 0 || q.p > 4 || !(q.dt > 0.0) || !std::isfinite(q.dt) ||
+      !(q.dx[0] > 0.0) || !(q.dx[1] > 0.0) || q.precision < FS_F64 || q.precision > FS_F32_TC_BF16X3 ||
+      q.lap < FS_LAP_SPECTRAL || q.lap > FS_LAP_FD4 || q.scheme < FS_SCHEME_SEMI_IMPLICIT_FS ||
+      q.scheme > FS_SCHEME_EXPLICIT_FD)
     return FS_ERR_INVALID_ARG;
+  // Valid requests outside this entry point's limits: FS_ERR_UNSUPPORTED.
+  if (q.ndim != 2 || (q.precision != FS_F64 && q.precision != FS_F32) || q.scheme != FS_SCHEME_SEMI_IMPLICIT_FS)
+    return FS_ERR_UNSUPPORTED;
   if (!pow2_between(q.n[0], 8, 1024) || !pow2_between(q.n[1], 8, 1024)) return FS_ERR_UNSUPPORTED;
   if ((long long)q.n[0] * q.n[1] > kMaxPoints || 1 + q.p > kMaxFields) return FS_ERR_UNSUPPORTED;
   if (nsteps == 0) return FS_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // The call copies its tables from one static host array and waits for the
+  // stream before it returns; neither may be recorded into a graph, so a
+  // capturing stream is refused (nothing is enqueued on it).
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return FS_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return FS_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FS_ERR_CUDA;
   if (!g_scratch_dev[dev]) {
@@ -244,7 +275,6 @@ extern "C" fs_status fs_step2d_static(const fs_params* prm, void* fields, int64_
     g_scratch_dev[dev] = ptr;
   }
   unsigned char* scratch = static_cast<unsigned char*>(g_scratch_dev[dev]);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   return q.precision == FS_F64 ? run_static<double>(q, fields, nsteps, s, scratch)
                                : run_static<float>(q, fields, nsteps, s, scratch);
 }

@@ -52,16 +52,8 @@ def library_path() -> str:
     return _build.LIB
 
 
-def lib(build_if_missing: bool = False):
-    """Load libfs_gb300.so (raises if it is not built)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if build_if_missing:
-        _build.build()
-    path = library_path()
-    if not os.path.exists(path):
-        raise FileNotFoundError(f"libfs_gb300.so is not built ({path}); run __graft_entry__.build()")
+def bind(path: str):
+    """Load a build of the library at `path` and declare the C signatures."""
     L = ctypes.CDLL(path)
     P = ctypes.POINTER(fs_params)
     plan = ctypes.c_void_p
@@ -86,6 +78,10 @@ def lib(build_if_missing: bool = False):
         "fs_last_launch_count": [plan, ctypes.POINTER(ctypes.c_int64)],
         "fs_destroy": [plan],
         "fs_step2d_static": [P, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
+        "fs_test_short_wait": [plan, ctypes.c_int],
+        "fs_set_pass_forms": [plan, ctypes.c_int, ctypes.c_int],
+        "fs_measure_fp64_rate": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -95,8 +91,21 @@ def lib(build_if_missing: bool = False):
     L.fs_last_error.restype = ctypes.c_char_p
     L.fs_version.argtypes = []
     L.fs_version.restype = ctypes.c_char_p
-    _lib = L
     return L
+
+
+def lib(build_if_missing: bool = False):
+    """Load libfs_gb300.so (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    path = library_path()
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"libfs_gb300.so is not built ({path}); run __graft_entry__.build()")
+    _lib = bind(path)
+    return _lib
 
 
 def _check(status: int, plan=None):
@@ -228,6 +237,24 @@ def fs_batch_schedule(plan):
     v = [ctypes.c_int64() for _ in range(4)]
     _check(lib().fs_batch_schedule(plan, *[ctypes.byref(x) for x in v]), plan)
     return tuple(x.value for x in v)
+
+
+def fs_set_pass_forms(plan, row_form: int, col_form: int):
+    """Kernel forms of the passes: 0 default, 1 half-length / tile, 2 warp per line."""
+    _check(lib().fs_set_pass_forms(plan, int(row_form), int(col_form)), plan)
+
+
+def fs_test_short_wait(plan, enable: bool):
+    """Test hook: cut the first bounded device wait of every pass short."""
+    _check(lib().fs_test_short_wait(plan, 1 if enable else 0), plan)
+
+
+def fs_measure_fp64_rate(stream=None):
+    """(DFMA, DADD) thread-instructions per second of the current device."""
+    s = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().fs_measure_fp64_rate(s, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def fs_workspace_bytes(plan) -> int:

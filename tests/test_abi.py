@@ -27,7 +27,7 @@ def declared_functions():
             continue
         txt = open(os.path.join(ROOT, "include", h)).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(fs_\w+)\s*\(", txt, flags=re.M)
+        names += re.findall(r"^\s*(?:FS_API\s+)?(?:const\s+)?\w+\s*\*?\s*(fs_\w+)\s*\(", txt, flags=re.M)
     return sorted(set(names))
 
 
@@ -36,6 +36,20 @@ def test_every_declared_symbol_is_exported(L):
     assert "fs_plan_create" in names and "fs_step" in names and len(names) >= 15
     for n in names:
         assert hasattr(L, n), n
+
+
+def test_only_the_c_abi_is_exported(L):
+    """Hidden visibility: the library exports the declared entry points and no
+    C++ symbol (template instantiations and their function-local statics stay
+    private, so a second build of the library in the same process, such as
+    the bounds-checked one, shares nothing with this one)."""
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True).stdout
+    syms = [l.split()[-1] for l in out.splitlines() if l.split()[-2:-1] in (["T"], ["u"], ["V"], ["W"])]
+    # weak instantiations of the C++ standard library's own templates keep the
+    # visibility its headers give them; none of them holds state of this library
+    ours = sorted(x for x in syms if not x.startswith(("_ZNSt", "_ZSt", "_ZNKSt")))
+    assert ours == declared_functions(), ours
 
 
 def test_version(L):

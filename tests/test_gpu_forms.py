@@ -1,0 +1,128 @@
+"""Both kernel forms of the FP32 passes against the FP64 oracle.
+
+Form 1: the half-length row pass (one real row as a complex line of nx/2) and
+the column-tile pass.  Form 2: the pair-form row pass (two rows as one complex
+line of nx) and the warp-per-column pass.  Both compute Algorithm 1; only the
+rounding order differs.  Each grid is run through the first step from the
+real fields (row mode 1), steady steps (mode 0) and the final inverse row pass
+(mode 2, fs_get_fields), for p = 0..4.
+
+Tolerance (relative L-inf per field): FP32 transforms of up to 1024 points,
+2e-6 per step (as the other FP32 parity tests), k steps 2e-6 * k * 2.
+"""
+import numpy as np
+import pytest
+
+from paper_2306_04322_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_04322_gb300 import build as B
+    from paper_2306_04322_gb300 import fs
+    B.build()
+    fs.lib()
+    return fs
+
+
+def rel_linf(a, b):
+    return max(np.max(np.abs(a[f] - b[f])) / max(np.max(np.abs(b[f])), 1e-300) for f in range(b.shape[0]))
+
+
+def bound(k):
+    return 2e-6 * k * 2.0
+
+
+def run(F, pr, f0, forms, chunks, precision="f32"):
+    import torch
+    plan = F.Plan(pr, precision)
+    F.fs_set_pass_forms(plan.h, *forms)
+    plan.set_fields(torch.tensor(f0, dtype=torch.float32, device="cuda"))
+    outs = []
+    for n in chunks:
+        plan.step(n)
+        outs.append(plan.get_fields().double().cpu().numpy())
+    plan.close()
+    return outs
+
+
+def covered(n, p):
+    nx, ny = n[0], n[1]
+    row = nx in (256, 512, 1024)
+    col = len(n) == 2 and ny in (256, 512, 1024)
+    return row, col
+
+
+@pytest.mark.parametrize("n,p", [
+    ((1024, 1024), 2), ((256, 512), 1), ((512, 256), 0), ((1024, 256), 2), ((256, 1024), 2),
+    ((1024, 64), 3), ((64, 1024), 2), ((512, 512), 4), ((256, 256), 3), ((256, 16, 16), 2), ((512, 8, 8), 1)])
+def test_forms_match_oracle(F, O, n, p):
+    pr = I.Problem(n=n, p=p)
+    pr.dt = 5.0 * I.fd_stable_dt(pr)
+    f0 = I.noise_fields(pr, seed=21)
+    r1, _ = O.step(pr, f0, 1)
+    r6, _ = O.step(pr, r1, 5)
+    row, col = covered(n, p)
+    results = {}
+    for forms in [(1, 1), (2 if row else 1, 2 if col else 1)]:
+        g1, g6 = run(F, pr, f0.astype(np.float32), forms, [1, 5])
+        e1, e6 = rel_linf(g1, r1), rel_linf(g6, r6)
+        print(f"{n} p={p} forms {forms}: 1 step {e1:.2e}, 6 steps {e6:.2e}")
+        assert e1 <= bound(1), (forms, e1)
+        assert e6 <= bound(6), (forms, e6)
+        results[forms] = g6
+    a, b = list(results.values())
+    assert rel_linf(a, b) <= bound(6)
+
+
+def test_pair_rows_under_the_tensor_core_columns(F, O):
+    """The tensor-core precisions keep their tile column pass and take the
+    pair-form rows."""
+    import torch
+    pr = I.Problem(n=(256, 256), p=2)
+    pr.dt = 5.0 * I.fd_stable_dt(pr)
+    f0 = I.noise_fields(pr, seed=22)
+    ref, _ = O.step(pr, f0, 3)
+    plan = F.Plan(pr, "tf32")
+    F.fs_set_pass_forms(plan.h, 2, 1)
+    plan.set_fields(torch.tensor(f0, dtype=torch.float32, device="cuda"))
+    plan.step(3)
+    got = plan.get_fields().double().cpu().numpy()
+    plan.close()
+    assert rel_linf(got, ref) <= 3e-5
+
+
+def test_form_selector_rejects_uncovered_grids(F):
+    import torch
+    pr = I.Problem(n=(128, 128), p=1)
+    pr.dt = 1e-3
+    plan = F.Plan(pr, "f32")
+    with pytest.raises(F.FSError) as ei:
+        F.fs_set_pass_forms(plan.h, 2, 2)
+    assert ei.value.status == F.FS_ERR_UNSUPPORTED
+    with pytest.raises(F.FSError) as ei:
+        F.fs_set_pass_forms(plan.h, 3, 0)
+    assert ei.value.status == F.FS_ERR_INVALID_ARG
+    plan.close()
+    plan = F.Plan(I.Problem(n=(256, 256), p=1, dt=1e-3), "f64")
+    with pytest.raises(F.FSError):
+        F.fs_set_pass_forms(plan.h, 2, 0)
+    plan.close()
+
+
+def test_forms_graph_path_headline(F, O):
+    """The benchmark's workload through the captured graph in both forms."""
+    pr = I.Problem(n=(1024, 1024), p=2)
+    pr.dt = 6.0 * I.fd_stable_dt(pr)
+    f0 = I.noise_fields(pr, seed=0)
+    ref, _ = O.step(pr, f0, 34)
+    for forms in [(1, 1), (2, 2), (2, 1), (1, 2)]:
+        (g,) = run(F, pr, f0.astype(np.float32), forms, [34])
+        e = rel_linf(g, ref)
+        print(f"1024^2 forms {forms}: 34 steps {e:.2e}")
+        assert e <= bound(34)
