@@ -194,11 +194,15 @@ FS_API fs_status fs_step_profiled(fs_plan_t plan, int64_t nsteps);
 FS_API fs_status fs_profile_read(fs_plan_t plan, double* ms_per_pass, int64_t* launches_per_pass, int npass_max,
                           int* npass);
 
-/* Batched plans: the persistent grid sizes (CTAs) of the row and column
- * launches chosen by the autotuner (it runs inside the first fs_set_fields
- * and times candidate grids on that state), and the work items of each. */
+/* Batched plans: the schedule the autotuner chose (it runs inside the first
+ * fs_set_fields and times candidates on that state): per pass the kernel
+ * form (1: half-length row pass / column tiles with radix-16 line
+ * transforms; 2: warp-per-line kernels, one warp per line with radix up to
+ * 32, two-column tiles -- FP32 members with both axes in [64, 1024]), the
+ * persistent grid size (CTAs) and the number of work items.  Any output
+ * pointer may be NULL. */
 FS_API fs_status fs_batch_schedule(fs_plan_t plan, int64_t* row_grid, int64_t* col_grid, int64_t* row_items,
-                            int64_t* col_items);
+                                   int64_t* col_items, int* row_form, int* col_form);
 
 /* Allocation-free 2D step, for callers that cannot allocate device memory:
  * a host program whose pool allocator owns all device memory before this
@@ -233,14 +237,23 @@ FS_API fs_status fs_batch_schedule(fs_plan_t plan, int64_t* row_grid, int64_t* c
 FS_API fs_status fs_step2d_static(const fs_params* prm, void* fields, int64_t nsteps, void* stream);
 
 /* Kernel forms of the passes (FP32 plans; the paper's method is the same
- * either way, the rounding order differs).  row_form / col_form: 0 = the
- * default (the warp-per-line form wherever it applies), 1 = the half-length
- * row pass / column-tile pass, 2 = the warp-per-line forms: the row pass
- * transforms two grid rows as one complex line (x lines of 256, 512 or 1024
- * points), the column pass gives each (column, field) its own warp (2D,
- * columns of 256, 512 or 1024 points).  Form 2 on a plan it does not
- * cover returns FS_ERR_UNSUPPORTED; FP64 plans always run form 1.  Used by
- * the tests (both forms against the oracle) and for A/B timing. */
+ * either way, the rounding order differs).  row_form / col_form:
+ *   1 = the half-length row pass (one real row as a complex line of nx/2)
+ *       and the column-tile pass (radix-16 line transforms);
+ *   2 = the warp-per-line forms: the row pass transforms two grid rows as
+ *       one complex line (x lines of 64 to 1024 points), the column pass
+ *       gives each (column, field) its own warp (2D columns of 64 to 1024
+ *       points);
+ *   3 = form 2 with two warps per line (lines of 128 to 1024 points, and
+ *       2D columns of 2048): half the values per thread, twice the warps;
+ *   0 = the default: form 2 for 2D lines of 256 to 1024 points, form 3 for
+ *       2D columns of 2048, form 1 otherwise (3D x passes, with their many
+ *       lines, keep form 1).
+ * Form 2 on a plan it does not cover returns FS_ERR_UNSUPPORTED; FP64 plans
+ * always run form 1.  On a batched plan a nonzero form pins the ensemble
+ * kernels' form for that pass (the autotuner then only picks the grid size,
+ * at the next fs_set_fields); 0 lets the autotuner choose.  Used by the
+ * tests (both forms against the oracle) and for A/B timing. */
 FS_API fs_status fs_set_pass_forms(fs_plan_t plan, int row_form, int col_form);
 
 /* Test hook of the failure-detection path (the paper has no counterpart).

@@ -39,6 +39,8 @@ struct KArgs {
   const void* tw_half;     // exp(-2 pi i k / nx), k = 0..nx/2-1 (real <-> half-length complex)
   const void* tw_row2;     // pass tables of the x line FFT of the pair form (L = nx, E = nx / 32; NULL: none)
   const void* tw_col2;     // pass tables of the y line FFT of the warp-per-column form (L = ny, E = ny / 32)
+  const void* tw_row2w;    // the same two with two warps per line (E = nx / 64, ny / 64; NULL: not this form)
+  const void* tw_col2w;
   const void* tc_b;        // tensor-core DFT stage: split 16-point DFT matrix, [hi | lo][32][32] float
   const void* k2x;         // |xi_x|^2 per x bin, nx/2 + 1 entries
   const void* k2y;         // |xi_y|^2 per y bin, ny entries
@@ -119,11 +121,27 @@ struct BatchArgs {
   long long row_total, col_total;
   long long row_grid, col_grid; // persistent grid sizes
   size_t row_smem, col_smem;
+  // warp-per-line forms (FP32 members with both axes in [64, 1024]; NULL / 0:
+  // not available): row-pair and (column pair, field group) work lists,
+  // two-column tensor maps
+  const CUtensorMap* maps2;
+  const long long* row2_begin;
+  const long long* col2_begin;
+  const int* col2_pairs;        // column pairs of each simulation
+  long long row2_total, col2_total;
+  long long row2_grid, col2_grid;
+  size_t row2_smem, col2_smem;
+  int row_form, col_form;       // chosen per pass: 1 half-length / tile kernels, 2 warp-per-line kernels
 };
 cudaError_t row_batch_launch_f32(const BatchArgs& b, cudaStream_t s);
 cudaError_t row_batch_launch_f64(const BatchArgs& b, cudaStream_t s);
 cudaError_t col_batch_launch_f32(const BatchArgs& b, cudaStream_t s);
 cudaError_t col_batch_launch_f64(const BatchArgs& b, cudaStream_t s);
+cudaError_t row2_batch_launch_f32(const BatchArgs& b, cudaStream_t s);
+cudaError_t col2_batch_launch_f32(const BatchArgs& b, cudaStream_t s);
+size_t row2_smem_f32(int nx, int nf);
+size_t col2_smem_f32(int ny);
+int col2_groups(int nf);
 size_t row_smem_f32(int nx, int nf);
 size_t row_smem_f64(int nx, int nf);
 long long row_blocks_f32(int nx, long long lines);

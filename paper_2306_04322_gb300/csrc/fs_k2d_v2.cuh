@@ -40,53 +40,68 @@ __device__ __forceinline__ void warp_line_fft(C (&v)[E], int t, const C* __restr
   else line_fft<L, E, DIR>(v, t, twp, st, ld, sync);
 }
 
-template <int NX>
+// G warps per line (1, or 2 to double the warps in flight when lines are
+// few); a line's TPL = 32 G threads hold E = NX / TPL values each.
+template <int NX, int G = 1>
 struct Row2Cfg {
-  static constexpr int E = NX / 32;                           // values per thread
+  static constexpr int TPL = 32 * G;                          // threads per line
+  static constexpr int E = NX / TPL;                          // values per thread
   static constexpr int H = NX / 2;                            // packed bins per row
   static constexpr int PL = (padded_len(NX) + 1) & ~1;        // complex per field area (16-byte multiple)
   static constexpr int TWS = pass_table_size(NX, E);
   static constexpr int TW_BYTES = ((TWS * 8) + 127) & ~127;
   static constexpr int BAR_BYTES = 128;
-  static constexpr int MAX_THREADS = 32 * 5;                  // one warp per field, nf <= 5
+  static constexpr int MAX_THREADS = TPL * 5;                 // one line per field, nf <= 5
 };
 
-template <int NX>
+template <int NX, int G = 1>
 constexpr size_t row2_smem_bytes(int nf) {
-  return Row2Cfg<NX>::BAR_BYTES + Row2Cfg<NX>::TW_BYTES + (size_t)(nf + 1) * Row2Cfg<NX>::PL * 8;
+  return Row2Cfg<NX, G>::BAR_BYTES + Row2Cfg<NX, G>::TW_BYTES + (size_t)(nf + 1) * Row2Cfg<NX, G>::PL * 8;
 }
 
-// One CTA per row pair (rows 2 blockIdx.x and 2 blockIdx.x + 1), one warp per
-// field.  Field areas [nf + 1][PL] (the last one holds df/dc): staging of the
-// bulk copies, then the warp's exchange buffer (pad32 layout), then the pair
-// values in natural order for the pointwise stage.
-template <int NX>
-__global__ void __launch_bounds__(Row2Cfg<NX>::MAX_THREADS, 3) fs_row2_kernel(KArgs a) {
+// Synchronisation of the threads of one line: the warp itself, or the two
+// warps of a line through named barrier 1 + line (64 threads).
+template <int G>
+struct LineSync {
+  int id;
+  __device__ __forceinline__ void operator()() const {
+    if constexpr (G == 1) __syncwarp();
+    else bar_sync(id, 32 * G);
+  }
+};
+
+// One row pair (rows 2 pair and 2 pair + 1) of the simulation `a`, one warp
+// per field (blockDim = 32 nf).  Field areas [nf + 1][PL] (the last one holds
+// df/dc): staging of the bulk copies, then the warp's exchange buffer (pad32
+// layout), then the pair values in natural order for the pointwise stage.
+// `bar` is an initialised mbarrier whose next phase has parity `parity`; the
+// ensemble kernel calls this once per work item.  Returns false if a bounded
+// wait gave up.
+template <int NX, int G = 1>
+__device__ __forceinline__ bool row2_body(const KArgs& a, long long pair, unsigned char* smem_raw, uint64_t* bar,
+                                          uint32_t parity) {
   using C = float2;
-  using Cfg = Row2Cfg<NX>;
-  constexpr int E = Cfg::E, H = Cfg::H, PL = Cfg::PL;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  using Cfg = Row2Cfg<NX, G>;
+  constexpr int E = Cfg::E, H = Cfg::H, PL = Cfg::PL, TPL = Cfg::TPL;
   C* tw = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);
   C* areas = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES + Cfg::TW_BYTES);
   const int nf = a.nf;
-  const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
-  const int nw = blockDim.x >> 5;  // = nf
-  const long long row0 = 2LL * blockIdx.x;  // row a; row b = row0 + 1
+  const int line = (threadIdx.x >> 5) / G, t = threadIdx.x % TPL;  // line of this thread, thread within it
+  const int nw = blockDim.x / TPL;  // lines per CTA = nf
+  const long long row0 = 2LL * pair;  // row a; row b = row0 + 1
+  const LineSync<G> lsync{1 + line};
   const bool from_real = (a.mode == 1);
 
   if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+    // the ensemble kernel reuses the areas: order the previous item's generic
+    // accesses (ended by the caller's CTA barrier) before the bulk writes
+    fence_proxy_async_smem();
     // both rows of a field are contiguous: NX complex (packed) or 2 NX reals
     const uint32_t bytes = (uint32_t)(NX * sizeof(C));
     const uint32_t tbytes = (uint32_t)(Cfg::TWS * sizeof(C));
     mbar_arrive_expect_tx(bar, tbytes + bytes * nf);
     // the constant pass table first, overlapping the previous grid's tail
-    bulk_g2s(tw, a.tw_row2, tbytes, bar);
+    bulk_g2s(tw, G == 1 ? a.tw_row2 : a.tw_row2w, tbytes, bar);
     griddep_wait();  // the spectra are the previous pass's output
     const C* spec = reinterpret_cast<const C*>(a.spec);
     const float* real = reinterpret_cast<const float*>(a.real);
@@ -99,15 +114,14 @@ __global__ void __launch_bounds__(Row2Cfg<NX>::MAX_THREADS, 3) fs_row2_kernel(KA
     }
   }
   griddep_launch_dependents();
-  if (!mbar_wait_bounded(bar, 0, first_wait_polls(a))) {
+  if (!mbar_wait_bounded(bar, parity, first_wait_polls(a))) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
-    mbar_wait_bounded(bar, 0, kWaitPolls);  // let the copies land before exiting
-    return;
+    mbar_wait_bounded(bar, parity, kWaitPolls);  // let the copies land before exiting
+    return false;
   }
 
   C* spec = reinterpret_cast<C*>(a.spec);
   float* real = reinterpret_cast<float*>(a.real);
-  auto wsync = []() { __syncwarp(); };
   bool bad = false;
   // Both transform phases share one FFT call site (the inverse is computed as
   // conj(FFT(conj(.)))): ph 0 inverse of the nf fields (modes 0, 2; mode 1
@@ -117,7 +131,7 @@ __global__ void __launch_bounds__(Row2Cfg<NX>::MAX_THREADS, 3) fs_row2_kernel(KA
     const bool inv = (ph == 0);
     const int f0 = inv ? 0 : (from_real ? 0 : 1);
     const int items = nf + 1 - f0 - (inv ? 1 : 0);  // inverse: fields 0..nf-1; forward: f0..nf
-    for (int i = w; i < items; i += nw) {
+    for (int i = line; i < items; i += nw) {
       const int f = f0 + i;
       C* s = areas + f * PL;
       auto st = [s](int q, C x) { s[pad32(q)] = x; };
@@ -130,19 +144,19 @@ __global__ void __launch_bounds__(Row2Cfg<NX>::MAX_THREADS, 3) fs_row2_kernel(KA
           float xa[E], xb[E];
 #pragma unroll
           for (int m = 0; m < E; ++m) {
-            xa[m] = r[t + 32 * m];
-            xb[m] = r[NX + t + 32 * m];
+            xa[m] = r[t + TPL * m];
+            xb[m] = r[NX + t + TPL * m];
           }
-          __syncwarp();
+          lsync();
 #pragma unroll
-          for (int m = 0; m < E; ++m) s[t + 32 * m] = make_float2(xa[m], xb[m]);
+          for (int m = 0; m < E; ++m) s[t + TPL * m] = make_float2(xa[m], xb[m]);
           continue;
         }
         // conj(Z), Z[k] = X_a[k] + i X_b[k]; staging: row a bins [0, H), row b [H, 2H);
         // bin 0 of a packed row holds (X[0], X[H]), both real
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-          const int k = t + 32 * m;
+          const int k = t + TPL * m;
           C z;
           if (k < H) {
             const C xa = s[k], xb = s[H + k];
@@ -155,40 +169,40 @@ __global__ void __launch_bounds__(Row2Cfg<NX>::MAX_THREADS, 3) fs_row2_kernel(KA
           }
           v[m] = cconj(z);
         }
-        __syncwarp();  // the staging area becomes the exchange buffer
+        lsync();  // the staging area becomes the exchange buffer
       } else {
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = s[t + 32 * m];  // z = g_a + i g_b, natural order
+        for (int m = 0; m < E; ++m) v[m] = s[t + TPL * m];  // z = g_a + i g_b, natural order
       }
-      warp_line_fft<NX, E, -1>(v, t, tw, st, ld, wsync);
+      warp_line_fft<NX, E, -1>(v, t, tw, st, ld, lsync);
       if (inv) {
         // a + i b = conj(v)
         if (a.mode == 2) {
           float* ra = real + f * a.npts + row0 * NX;
 #pragma unroll
           for (int m = 0; m < E; ++m) {
-            const int n = t + 32 * m;
+            const int n = t + TPL * m;
             if (real_ok(a, &ra[n], 4)) ra[n] = v[m].x;
             if (real_ok(a, &ra[NX + n], 4)) ra[NX + n] = -v[m].y;
           }
         } else {
-          __syncwarp();
+          lsync();
 #pragma unroll
-          for (int m = 0; m < E; ++m) s[t + 32 * m] = cconj(v[m]);
+          for (int m = 0; m < E; ++m) s[t + TPL * m] = cconj(v[m]);
         }
       } else {
         // separate the two rows' spectra; Z[nx - k] through shared memory
-        __syncwarp();
+        lsync();
 #pragma unroll
-        for (int m = 0; m < E; ++m) s[t + 32 * m] = v[m];
-        __syncwarp();
+        for (int m = 0; m < E; ++m) s[t + TPL * m] = v[m];
+        lsync();
         const bool c_carried = (f == 0);  // mode 1: c stored as x spectrum / nx
         const float cs = c_carried ? 0.5f / (float)NX : 1.0f;
         C* Pa = spec + f * a.slot_stride + row0 * H;
         C* Pb = Pa + H;
 #pragma unroll
         for (int m = 0; m < E / 2; ++m) {
-          const int k = t + 32 * m;
+          const int k = t + TPL * m;
           const C zk = v[m];
           C pa, pb;
           if (k == 0) {
@@ -210,7 +224,7 @@ __global__ void __launch_bounds__(Row2Cfg<NX>::MAX_THREADS, 3) fs_row2_kernel(KA
       }
     }
     if (!inv) break;
-    if (a.mode == 2) return;
+    if (a.mode == 2) return true;
     __syncthreads();
 
     // pointwise stage: pairs (row a, row b) of every field, lane-wise
@@ -237,11 +251,25 @@ __global__ void __launch_bounds__(Row2Cfg<NX>::MAX_THREADS, 3) fs_row2_kernel(KA
     __syncthreads();
   }
   if (bad) atomicOr(a.flag, FS_FLAG_NONFINITE);
+  return true;
 }
 
-template <int NY>
+template <int NX, int G>
+__global__ void __launch_bounds__(Row2Cfg<NX, G>::MAX_THREADS, G == 1 ? 3 : 2) fs_row2_kernel(KArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  row2_body<NX, G>(a, blockIdx.x, smem_raw, bar, 0);
+}
+
+template <int NY, int G = 1>
 struct Col2Cfg {
-  static constexpr int E = NY / 32;
+  static constexpr int TPL = 32 * G;                          // threads per line
+  static constexpr int E = NY / TPL;
   static constexpr int TK = 2;                                // kx columns per CTA
   static constexpr int BH = NY < 256 ? NY : 256;              // TMA box height (rows)
   static constexpr int PL = (padded_len(NY) + 1) & ~1;        // complex per compact column area
@@ -253,12 +281,14 @@ struct Col2Cfg {
   static constexpr int TW_BYTES = ((TWS * 8) + 127) & ~127;
   static constexpr int K2_BYTES = ((NY * 4) + 127) & ~127;
   static constexpr int HEAD = 128 + TW_BYTES + K2_BYTES;
+  // CTAs per SM the registers are budgeted for: 128 per thread at 32 values
+  static constexpr int MIN_BLOCKS = E >= 32 ? 4 / G : (G == 1 ? 4 : 3);
 };
 
 // Shared memory of one CTA: the head and two slot regions.
-template <int NY>
+template <int NY, int G = 1>
 constexpr size_t col2_smem_bytes() {
-  return Col2Cfg<NY>::HEAD + (size_t)2 * Col2Cfg<NY>::SLOT * 8;
+  return Col2Cfg<NY, G>::HEAD + (size_t)2 * Col2Cfg<NY, G>::SLOT * 8;
 }
 
 // The packed kx = 0 / Nyquist column of the first CTA: y holds this warp's
@@ -268,17 +298,17 @@ constexpr size_t col2_smem_bytes() {
 // (Eqs. A-C_discrete_fft_c / _eta) and repacked, in place.  The update maps
 // each pair {ky, ny - ky} onto itself (A(ny - ky) = conj A(ky), the same for
 // B, and the update is real-linear with the same K2 at ky and ny - ky), so a
-// lane owns both entries of its pairs and no other lane touches them.  Two
-// warps of the grid run this, so it stays out of line and rolled.
-template <int NY>
+// thread owns both entries of its pairs and no other thread touches them.  A
+// few warps of the grid run this, so it stays out of line and rolled.
+template <int NY, int TPL>
 __device__ __noinline__ void col2_packed_update(float2* __restrict__ y, const float2* __restrict__ fz, int t,
                                                 bool isC, KUpdate<float> up, float kx2, float kxn2,
                                                 const float* __restrict__ k2yt, const double* csum,
                                                 double inv_npts) {
   using C = float2;
 #pragma unroll 1
-  for (int m = 0; m <= NY / 64; ++m) {
-    const int ky = t + 32 * m;  // pairs ky = 0 .. ny/2
+  for (int m = 0; m <= NY / (2 * TPL); ++m) {
+    const int ky = t + TPL * m;  // pairs ky = 0 .. ny/2
     if (ky > NY / 2) break;
     const int kq = (NY - ky) & (NY - 1);
     const float ky2 = k2yt[ky];
@@ -310,67 +340,66 @@ __device__ __noinline__ void col2_packed_update(float2* __restrict__ y, const fl
 // transform the results go back to the interleaved tile layout and out by
 // TMA, so the global writes are whole 16-byte rows instead of one 8-byte
 // value per lane and row.
-template <int NY>
-__global__ void __launch_bounds__(128, 4) fs_col2_kernel(KArgs a, const __grid_constant__ CUtensorMap tmap) {
+// Column pair `cpair`, field group `group` of the simulation `a` (blockDim =
+// 128); `bar` as for row2_body.  Returns false if a bounded wait gave up.
+template <int NY, int G = 1>
+__device__ __forceinline__ bool col2_body(const KArgs& a, const CUtensorMap* tmap, int cpair, int group,
+                                          unsigned char* smem_raw, uint64_t* bar, uint32_t parity) {
   using C = float2;
-  using Cfg = Col2Cfg<NY>;
-  constexpr int E = Cfg::E, BH = Cfg::BH, PL = Cfg::PL, SLOT = Cfg::SLOT;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  using Cfg = Col2Cfg<NY, G>;
+  constexpr int E = Cfg::E, BH = Cfg::BH, PL = Cfg::PL, SLOT = Cfg::SLOT, TPL = Cfg::TPL;
   C* tw = reinterpret_cast<C*>(smem_raw + 128);
   float* k2yt = reinterpret_cast<float*>(smem_raw + 128 + Cfg::TW_BYTES);
   C* regions = reinterpret_cast<C*>(smem_raw + Cfg::HEAD);
   const int nf = a.nf, p = nf - 1;
-  const int group = blockIdx.y;
-  const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
-  const int j = w & 1, r = w >> 1;
+  const int line = (threadIdx.x >> 5) / G, t = threadIdx.x % TPL;  // line (region, column), thread in it
+  const int j = line & 1, r = line >> 1;
   const int nreg = group == 0 ? 2 : (p - 2 * (group - 1) >= 2 ? 2 : 1);
   // slot of region q of this group: group 0: df/dc (nf), c (0); else eta_{2g-1+q}
   auto slot_of = [nf, group](int q) { return group == 0 ? (q == 0 ? nf : 0) : 2 * group - 1 + q; };
   const bool isF = (group == 0 && r == 0), isC = (group == 0 && r == 1);
-  const int kx0 = blockIdx.x * Cfg::TK, kx = kx0 + j;
+  const int kx0 = cpair * Cfg::TK, kx = kx0 + j;
   const int H = a.nx / 2;
 
+  if (r >= nreg) return true;  // the second region of a last group with one eta
   if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (r >= nreg) return;  // the second region of a last group with one eta
-  if (threadIdx.x == 0) {
+    // the ensemble kernel reuses the regions: order the previous item's
+    // generic accesses (ended by the caller's CTA barrier) before the TMA writes
+    fence_proxy_async_smem();
     const uint32_t tbytes = (uint32_t)(Cfg::TWS * sizeof(C)), kbytes = (uint32_t)(NY * sizeof(float));
     mbar_arrive_expect_tx(bar, tbytes + kbytes + (uint32_t)(nreg * NY * Cfg::TK * sizeof(C)));
     // the constant tables first, overlapping the previous grid's tail
-    bulk_g2s(tw, a.tw_col2, tbytes, bar);
+    bulk_g2s(tw, G == 1 ? a.tw_col2 : a.tw_col2w, tbytes, bar);
     bulk_g2s(k2yt, a.k2y, kbytes, bar);
     griddep_wait();  // the tiles are the previous pass's output
     for (int q = 0; q < nreg; ++q)
       // innermost coordinate kx0 (8-byte units) is even: 16-byte aligned
       for (int y0 = 0; y0 < NY; y0 += BH)
-        tma_load_3d(regions + q * SLOT + y0 * Cfg::TK, &tmap, kx0, y0, slot_of(q), bar);
+        tma_load_3d(regions + q * SLOT + y0 * Cfg::TK, tmap, kx0, y0, slot_of(q), bar);
   }
   const float* __restrict__ k2xt = reinterpret_cast<const float*>(a.k2x);
   const float kx2 = k2xt[kx];
   griddep_launch_dependents();
-  if (!mbar_wait_bounded(bar, 0, first_wait_polls(a))) {
+  if (!mbar_wait_bounded(bar, parity, first_wait_polls(a))) {
     if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
-    mbar_wait_bounded(bar, 0, kWaitPolls);
-    return;
+    mbar_wait_bounded(bar, parity, kWaitPolls);
+    return false;
   }
 
   C* reg = regions + r * SLOT;
   C v[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) v[m] = reg[(t + 32 * m) * Cfg::TK + j];
+  for (int m = 0; m < E; ++m) v[m] = reg[(t + TPL * m) * Cfg::TK + j];
   // named barriers with compile-time ids: 1, 2 per region (its two column
-  // warps), 3, 4 per column (df/dc^ handed to the c warp)
-  auto region_sync = [r]() { if (r == 0) bar_sync(1, 64); else bar_sync(2, 64); };
+  // lines), 3, 4 per column (df/dc^ handed to the c line), 5.. per line (its
+  // G warps, G = 2)
+  auto region_sync = [r]() { if (r == 0) bar_sync(1, 64 * G); else bar_sync(2, 64 * G); };
+  const LineSync<G> lsync{5 + line};
   // both columns of this region have left the tile: it becomes two compact areas
   region_sync();
   C* xa = reg + j * PL;
   auto st = [xa](int q, C x) { xa[pad32(q)] = x; };
   auto ld = [xa](int q) { return xa[pad32(q)]; };
-  auto wsync = []() { __syncwarp(); };
   const KUpdate<float> up(a);
   const bool special = (kx0 == 0 && j == 0);  // the packed kx = 0 / Nyquist column
   const C* fz = regions + j * PL;             // df/dc^ of this column (region 0 of group 0)
@@ -378,28 +407,28 @@ __global__ void __launch_bounds__(128, 4) fs_col2_kernel(KArgs a, const __grid_c
   // One FFT call site: it 0 forward (all warps), it 1 inverse (c, eta) as
   // conj(FFT(conj(.))).
   for (int it = 0; it < 2; ++it) {
-    warp_line_fft<NY, E, -1>(v, t, tw, st, ld, wsync);
+    warp_line_fft<NY, E, -1>(v, t, tw, st, ld, lsync);
     if (it == 1) break;
     if (isF) {
       // df/dc^: natural layout for the c warp of this column
-      __syncwarp();
+      lsync();
 #pragma unroll
-      for (int m = 0; m < E; ++m) xa[t + 32 * m] = v[m];
-      if (j == 0) bar_arrive(3, 64); else bar_arrive(4, 64);
-      return;
+      for (int m = 0; m < E; ++m) xa[t + TPL * m] = v[m];
+      if (j == 0) bar_arrive(3, 64 * G); else bar_arrive(4, 64 * G);
+      return true;
     }
     if (isC) {
-      if (j == 0) bar_sync(3, 64); else bar_sync(4, 64);
+      if (j == 0) bar_sync(3, 64 * G); else bar_sync(4, 64 * G);
     }
     if (special) {
-      __syncwarp();
+      lsync();
 #pragma unroll
-      for (int m = 0; m < E; ++m) xa[t + 32 * m] = v[m];
-      __syncwarp();
-      col2_packed_update<NY>(xa, fz, t, isC, up, kx2, k2xt[H], k2yt, a.csum, a.inv_npts);
-      __syncwarp();
+      for (int m = 0; m < E; ++m) xa[t + TPL * m] = v[m];
+      lsync();
+      col2_packed_update<NY, TPL>(xa, fz, t, isC, up, kx2, k2xt[H], k2yt, a.csum, a.inv_npts);
+      lsync();
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = cconj(xa[t + 32 * m]);
+      for (int m = 0; m < E; ++m) v[m] = cconj(xa[t + TPL * m]);
     } else {
       // c^' = (c^ - M dt K2 f^) / (1 + M dt kappa_c K2^2), eta^' = g^ / (1 + L dt kappa_eta K2)
       // (scales folded as in KUpdate); one code path for both, the quotient by
@@ -409,7 +438,7 @@ __global__ void __launch_bounds__(128, 4) fs_col2_kernel(KArgs a, const __grid_c
       const float bk = isC ? up.Mdt_c : 0.f;
 #pragma unroll
       for (int m = 0; m < E; ++m) {
-        const int ky = t + 32 * m;
+        const int ky = t + TPL * m;
         const float k2 = kx2 + k2yt[ky];
         const float d = __fdividef(num, fmaf(qk, isC ? k2 * k2 : k2, 1.f));
         const C zf = isC ? fz[ky] : make_float2(0.f, 0.f);
@@ -421,35 +450,49 @@ __global__ void __launch_bounds__(128, 4) fs_col2_kernel(KArgs a, const __grid_c
   // of this region, then out by TMA: c -> slot 0, eta_i -> slot i
   region_sync();  // both columns are done with their compact areas
 #pragma unroll
-  for (int m = 0; m < E; ++m) reg[(t + 32 * m) * Cfg::TK + j] = cconj(v[m]);
+  for (int m = 0; m < E; ++m) reg[(t + TPL * m) * Cfg::TK + j] = cconj(v[m]);
   fence_proxy_async_smem();
   region_sync();
-  if (j == 0 && t == 0) {
-    for (int y0 = 0; y0 < NY; y0 += BH) tma_store_3d(&tmap, kx0, y0, slot_of(r), reg + y0 * Cfg::TK);
+  if (j == 0 && t == 0) {  // one thread of the region's column-0 line
+    for (int y0 = 0; y0 < NY; y0 += BH) tma_store_3d(tmap, kx0, y0, slot_of(r), reg + y0 * Cfg::TK);
     bulk_commit();
-    bulk_wait_all();
+    bulk_wait_all();  // the tile is read (and written out) before the region is reused or the CTA exits
   }
+  return true;
+}
+
+template <int NY, int G>
+__global__ void __launch_bounds__(128 * G, Col2Cfg<NY, G>::MIN_BLOCKS)
+    fs_col2_kernel(KArgs a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  col2_body<NY, G>(a, &tmap, blockIdx.x, blockIdx.y, smem_raw, bar, 0);
 }
 
 // Launchers: cudaErrorNotSupported when this form does not cover the
 // request (the caller falls back to the half-length / tile kernels).
-template <int NX>
+template <int NX, int G>
 cudaError_t row2_launch_n(const KArgs& a, cudaStream_t s) {
   static unsigned done = 0;
-  cudaError_t e = allow_big_smem(fs_row2_kernel<NX>, &done);
+  cudaError_t e = allow_big_smem(fs_row2_kernel<NX, G>, &done);
   if (e != cudaSuccess) return e;
-  return launch_pdl(fs_row2_kernel<NX>, dim3((unsigned)(a.lines / 2)), dim3((unsigned)(32 * a.nf)),
-                    row2_smem_bytes<NX>(a.nf), s, a);
+  return launch_pdl(fs_row2_kernel<NX, G>, dim3((unsigned)(a.lines / 2)), dim3((unsigned)(32 * G * a.nf)),
+                    row2_smem_bytes<NX, G>(a.nf), s, a);
 }
 
-template <int NY>
+template <int NY, int G>
 cudaError_t col2_launch_n(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
   static unsigned done = 0;
-  cudaError_t e = allow_big_smem(fs_col2_kernel<NY>, &done);
+  cudaError_t e = allow_big_smem(fs_col2_kernel<NY, G>, &done);
   if (e != cudaSuccess) return e;
   const unsigned groups = (unsigned)(1 + (a.nf - 1 + 1) / 2);  // {df/dc, c} and the eta pairs
-  return launch_pdl(fs_col2_kernel<NY>, dim3((unsigned)(a.nx / 2 / Col2Cfg<NY>::TK), groups), dim3(128u),
-                    col2_smem_bytes<NY>(), s, a, tm);
+  return launch_pdl(fs_col2_kernel<NY, G>, dim3((unsigned)(a.nx / 2 / Col2Cfg<NY, G>::TK), groups),
+                    dim3((unsigned)(128 * G)), col2_smem_bytes<NY, G>(), s, a, tm);
 }
 
 }  // namespace fs

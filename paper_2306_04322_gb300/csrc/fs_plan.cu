@@ -40,7 +40,9 @@ struct Member {
   void* tw_row_w = nullptr;  // x-pass tables with 32 values per thread (FP32 rows of 1024)
   void* tc_b = nullptr;  // split DFT matrix of the tensor-core stage (TC precisions)
   void* tw_row2 = nullptr;  // x-line tables of the pair-form row pass (FP32, nx in {256, 512, 1024})
-  void* tw_col2 = nullptr;  // y-line tables of the warp-per-column pass (FP32 2D, ny in {256, 512, 1024})
+  void* tw_col2 = nullptr;  // y-line tables of the warp-per-column pass (FP32 2D, ny in [64, 1024])
+  void* tw_row2w = nullptr; // the same with two warps per line (lines of 128 points and more)
+  void* tw_col2w = nullptr;
   double* csum = nullptr;
   long long slot_stride = 0;
   CUtensorMap tmap_col;  // [slot * nz + z][y][kx] tiles of the 2D column pass / 3D y passes
@@ -81,7 +83,8 @@ struct fs_plan {
   int gsteps = 0;
   int64_t last_launches = 0;
   int short_wait = 0;  // test hook of fs_test_short_wait
-  int row_form = 0;    // fs_set_pass_forms: 0 default, 1 half-length / tile kernels, 2 warp-per-line kernels
+  int row_form = 0;    // fs_set_pass_forms: 0 default, 1 half-length / tile kernels, 2 warp-per-line
+                       // kernels, 3 the same with two warps per line
   int col_form = 0;
   std::vector<cudaEvent_t> ev_pool;  // fs_step_profiled timing events
   std::vector<int> ev_kind;
@@ -249,8 +252,19 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   a.tw_z = m.tw_z;
   a.tw_half = m.tw_half;
   a.tw_row_w = m.tw_row_w;
-  a.tw_row2 = (p->row_form == 1) ? nullptr : m.tw_row2;
-  a.tw_col2 = (p->col_form == 1) ? nullptr : m.tw_col2;
+  // single plans: the warp-per-line forms by default for lines of 256 points
+  // and more (form 0) -- rows only in 2D: a 3D x pass has ny nz lines, and
+  // one row pair per CTA (table fetch and set-up per pair) loses to the
+  // several-row CTAs of the half-length kernel there -- always with form 2,
+  // never with form 1; ensemble members keep both tables (the autotuner
+  // picks the form per pass)
+  const bool r2 = p->batch || p->row_form == 2 || (p->row_form == 0 && m.prm.n[0] >= 256 && m.prm.ndim == 2);
+  const bool c2 = p->batch || p->col_form == 2 || (p->col_form == 0 && m.prm.n[1] >= 256);
+  a.tw_row2 = r2 ? m.tw_row2 : nullptr;
+  a.tw_col2 = c2 ? m.tw_col2 : nullptr;
+  a.tw_row2w = (!p->batch && p->row_form == 3) ? m.tw_row2w : nullptr;
+  // columns of 2048 points have only the two-warp form, the default there
+  a.tw_col2w = (!p->batch && (p->col_form == 3 || (p->col_form == 0 && m.prm.n[1] == 2048))) ? m.tw_col2w : nullptr;
   a.tc_b = m.tc_b;
   a.k2x = m.k2x;
   a.k2y = m.k2y;
@@ -293,14 +307,14 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
 // FP32 plans take the warp-per-line forms where they apply (KArgs::tw_row2 /
 // tw_col2 set), else the half-length row / tile column kernels.
 cudaError_t launch_row(const fs_plan* p, const fs::KArgs& a, cudaStream_t s) {
-  if (!p->f64 && a.tw_row2) {
+  if (!p->f64 && (a.tw_row2 || a.tw_row2w)) {
     cudaError_t e = fs::row2_launch_f32(a, s);
     if (e != cudaErrorNotSupported) return e;
   }
   return p->f64 ? fs::row_launch_f64(a, s) : fs::row_launch_f32(a, s);
 }
 cudaError_t launch_col(const fs_plan* p, const Member& m, const fs::KArgs& a, cudaStream_t s) {
-  if (!p->f64 && a.tw_col2) {
+  if (!p->f64 && (a.tw_col2 || a.tw_col2w)) {
     cudaError_t e = fs::col2_launch_f32(a, m.tmap_col2, s);
     if (e != cudaErrorNotSupported) return e;
   }
@@ -333,6 +347,7 @@ EncodeTiledFn encode_tiled() {
 bool row2_form(const fs_params& prm, bool f64) {
   return !f64 && prm.scheme == FS_SCHEME_SEMI_IMPLICIT_FS && fs::row2_supported(prm.n[0], 1 + prm.p);
 }
+// (columns of 2048 points: two warps per line only)
 bool col2_form(const fs_params& prm, bool f64) {
   return !f64 && prm.scheme == FS_SCHEME_SEMI_IMPLICIT_FS && prm.ndim == 2 && prm.precision == FS_F32 &&
          fs::col2_supported(prm.n[1], 1 + prm.p);
@@ -403,7 +418,11 @@ void* fd_scratch(const fs_plan* p, const Member& m) {
 cudaError_t launch_batch_pass(const fs_plan* p, int mode, int kind, cudaStream_t s) {
   fs::BatchArgs b = p->bargs;
   if (mode == 1) b.mem = p->bmem1;
-  if (kind == 0) return p->f64 ? fs::row_batch_launch_f64(b, s) : fs::row_batch_launch_f32(b, s);
+  if (kind == 0) {
+    if (b.row_form == 2) return fs::row2_batch_launch_f32(b, s);
+    return p->f64 ? fs::row_batch_launch_f64(b, s) : fs::row_batch_launch_f32(b, s);
+  }
+  if (b.col_form == 2) return fs::col2_batch_launch_f32(b, s);
   return p->f64 ? fs::col_batch_launch_f64(b, s) : fs::col_batch_launch_f32(b, s);
 }
 
@@ -510,11 +529,13 @@ fs_status read_flag(fs_plan* p) {
 //   tw_half[nx/2]                           (exp(-2 pi i k / nx), complex)
 //   tc_b[2048] (TC precisions only)         (split DFT matrix of the tensor-core stage, 32-bit words)
 struct TableLayout {
-  size_t k2x, k2y, k2z, tw_row, tw_row_w, tw_col, tw_z, tw_half, tc_b, tw_row2, tw_col2, total;  // offsets (bytes)
+  size_t k2x, k2y, k2z, tw_row, tw_row_w, tw_col, tw_z, tw_half, tc_b, tw_row2, tw_col2, tw_row2w, tw_col2w,
+      total;  // offsets (bytes)
   int Lrow, Erow, Lcol, Ecol, Lz, Ez;
 };
 
 size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+size_t align128(size_t v) { return (v + 127) & ~(size_t)127; }
 
 // Tensor-core DFT stage of a precision (the device's TC mode numbers):
 // 0 none, 1 TF32 x 3, 2 BF16 x 3.
@@ -624,8 +645,12 @@ TableLayout table_layout(const fs_params& prm, bool f64) {
   o = align16(o + (tc_split(prm.precision) ? 2048 * sizeof(float) : 0));
   t.tw_row2 = o;  // pair-form row pass: L = nx, E = nx / 32
   o = align16(o + (row2_form(prm, f64) ? cs * fs::pass_table_size(nx, nx / 32) : 0));
-  t.tw_col2 = o;  // warp-per-column pass: L = ny, E = ny / 32
-  o = align16(o + (col2_form(prm, f64) ? cs * fs::pass_table_size(ny, ny / 32) : 0));
+  t.tw_col2 = o;  // warp-per-column pass: L = ny, E = ny / 32 (up to 1024 points)
+  o = align16(o + (col2_form(prm, f64) && ny <= 1024 ? cs * fs::pass_table_size(ny, ny / 32) : 0));
+  t.tw_row2w = o;  // two warps per line: E = nx / 64, ny / 64
+  o = align16(o + (row2_form(prm, f64) && nx >= 128 ? cs * fs::pass_table_size(nx, nx / 64) : 0));
+  t.tw_col2w = o;
+  o = align16(o + (col2_form(prm, f64) && ny >= 128 ? cs * fs::pass_table_size(ny, ny / 64) : 0));
   t.total = o;
   return t;
 }
@@ -675,9 +700,11 @@ cudaError_t upload_tables(Member& m, bool f64, char* dev, size_t bytes) {
   for (int k = 0; k <= nx / 2; ++k) kx[k] = axis_k2(prm.lap, k, nx, prm.dx[0]);
   for (int k = 0; k < ny; ++k) ky[k] = axis_k2(prm.lap, k, ny, prm.dx[1]);
   for (int k = 0; k < nz && prm.ndim > 2; ++k) kz[k] = axis_k2(prm.lap, k, nz, prm.dx[2]);
-  std::vector<long double> rr, ii, wr, wi, cr, ci, zr, zi, hr, hi, r2r, r2i, c2r, c2i;
+  std::vector<long double> rr, ii, wr, wi, cr, ci, zr, zi, hr, hi, r2r, r2i, c2r, c2i, r3r, r3i, c3r, c3i;
   if (row2_form(prm, f64)) pass_table(nx, nx / 32, r2r, r2i);
-  if (col2_form(prm, f64)) pass_table(ny, ny / 32, c2r, c2i);
+  if (col2_form(prm, f64) && ny <= 1024) pass_table(ny, ny / 32, c2r, c2i);
+  if (row2_form(prm, f64) && nx >= 128) pass_table(nx, nx / 64, r3r, r3i);
+  if (col2_form(prm, f64) && ny >= 128) pass_table(ny, ny / 64, c3r, c3i);
   pass_table(t.Lrow, t.Erow, rr, ii);
   if (wide_rows(prm, f64)) pass_table(t.Lrow, 32, wr, wi);
   pass_table(t.Lcol, t.Ecol, cr, ci);
@@ -707,6 +734,8 @@ cudaError_t upload_tables(Member& m, bool f64, char* dev, size_t bytes) {
     put_cplx<float>(buf, t.tw_half, hr, hi);
     put_cplx<float>(buf, t.tw_row2, r2r, r2i);
     put_cplx<float>(buf, t.tw_col2, c2r, c2i);
+    put_cplx<float>(buf, t.tw_row2w, r3r, r3i);
+    put_cplx<float>(buf, t.tw_col2w, c3r, c3i);
   }
   m.k2x = dev + t.k2x;
   m.k2y = dev + t.k2y;
@@ -717,7 +746,9 @@ cudaError_t upload_tables(Member& m, bool f64, char* dev, size_t bytes) {
   m.tw_z = dev + t.tw_z;
   m.tw_half = dev + t.tw_half;
   m.tw_row2 = row2_form(prm, f64) ? dev + t.tw_row2 : nullptr;
-  m.tw_col2 = col2_form(prm, f64) ? dev + t.tw_col2 : nullptr;
+  m.tw_col2 = col2_form(prm, f64) && ny <= 1024 ? dev + t.tw_col2 : nullptr;
+  m.tw_row2w = row2_form(prm, f64) && nx >= 128 ? dev + t.tw_row2w : nullptr;
+  m.tw_col2w = col2_form(prm, f64) && ny >= 128 ? dev + t.tw_col2w : nullptr;
   if (const int mode = tc_split(prm.precision)) {
     tc_table(mode, reinterpret_cast<uint32_t*>(buf.data() + t.tc_b));
     m.tc_b = dev + t.tc_b;
@@ -752,6 +783,14 @@ fs_status setup_batch(fs_plan* p) {
   std::vector<long long> rb(nm + 1, 0), cb(nm + 1, 0);
   std::vector<int> tiles(nm);
   size_t rsm = 0, csm = 0;
+  // warp-per-line form: every member FP32 with both axes in [64, 1024]
+  bool v2 = !p->f64;
+  for (const Member& m : p->members) v2 = v2 && m.tw_row2 && m.tw_col2;
+  std::vector<CUtensorMap> maps2(nm);
+  std::vector<long long> rb2(nm + 1, 0), cb2(nm + 1, 0);
+  std::vector<int> pairs2(nm, 0);
+  size_t rsm2 = 0, csm2 = 0;
+  p->batch = true;  // make_args: ensemble members keep both forms' tables
   for (int e = 0; e < nm; ++e) {
     const Member& m = p->members[order[e]];
     const int nx = m.prm.n[0], ny = m.prm.n[1];
@@ -765,13 +804,27 @@ fs_status setup_batch(fs_plan* p) {
     cb[e + 1] = cb[e] + (long long)tiles[e] * p->nf;
     rsm = std::max(rsm, p->f64 ? fs::row_smem_f64(nx, p->nf) : fs::row_smem_f32(nx, p->nf));
     csm = std::max(csm, p->f64 ? fs::col_smem_f64(ny, tk) : fs::col_smem_f32(ny, tk));
+    if (v2) {
+      maps2[e] = m.tmap_col2;
+      pairs2[e] = nx / 4;  // nx / 2 columns, two per item
+      rb2[e + 1] = rb2[e] + ny / 2;
+      cb2[e + 1] = cb2[e] + (long long)pairs2[e] * fs::col2_groups(p->nf);
+      rsm2 = std::max(rsm2, fs::row2_smem_f32(nx, p->nf));
+      csm2 = std::max(csm2, fs::col2_smem_f32(ny));
+    }
   }
   const size_t o_maps = 0, o_k0 = align16(o_maps + sizeof(CUtensorMap) * nm);
   const size_t o_k1 = align16(o_k0 + sizeof(fs::KArgs) * nm), o_rb = align16(o_k1 + sizeof(fs::KArgs) * nm);
   const size_t o_cb = align16(o_rb + sizeof(long long) * (nm + 1));
-  const size_t o_t = align16(o_cb + sizeof(long long) * (nm + 1)), total = align16(o_t + sizeof(int) * nm);
+  // tensor maps read by TMA from global memory must be 64-byte aligned: both
+  // map arrays start on 128 bytes (the block itself is 256-byte aligned)
+  const size_t o_t = align16(o_cb + sizeof(long long) * (nm + 1)), o_m2 = align128(o_t + sizeof(int) * nm);
+  const size_t o_rb2 = align16(o_m2 + sizeof(CUtensorMap) * nm), o_cb2 = align16(o_rb2 + sizeof(long long) * (nm + 1));
+  const size_t o_p2 = align16(o_cb2 + sizeof(long long) * (nm + 1)), total = align16(o_p2 + sizeof(int) * nm);
   char* dev = (char*)plan_alloc(p, total);
   if (!dev) return fail(nullptr, FS_ERR_OOM, "device workspace allocation failed");
+  if (((uintptr_t)(dev + o_maps) % 64) || ((uintptr_t)(dev + o_m2) % 64))
+    return fail(nullptr, FS_ERR_CUDA, "tensor maps of the ensemble are not 64-byte aligned");
   std::vector<char> host(total, 0);
   std::memcpy(host.data() + o_maps, maps.data(), sizeof(CUtensorMap) * nm);
   std::memcpy(host.data() + o_k0, k0.data(), sizeof(fs::KArgs) * nm);
@@ -779,6 +832,10 @@ fs_status setup_batch(fs_plan* p) {
   std::memcpy(host.data() + o_rb, rb.data(), sizeof(long long) * (nm + 1));
   std::memcpy(host.data() + o_cb, cb.data(), sizeof(long long) * (nm + 1));
   std::memcpy(host.data() + o_t, tiles.data(), sizeof(int) * nm);
+  std::memcpy(host.data() + o_m2, maps2.data(), sizeof(CUtensorMap) * nm);
+  std::memcpy(host.data() + o_rb2, rb2.data(), sizeof(long long) * (nm + 1));
+  std::memcpy(host.data() + o_cb2, cb2.data(), sizeof(long long) * (nm + 1));
+  std::memcpy(host.data() + o_p2, pairs2.data(), sizeof(int) * nm);
   cudaError_t e = cudaMemcpy(dev, host.data(), total, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch tables");
   fs::BatchArgs& b = p->bargs;
@@ -797,50 +854,90 @@ fs_status setup_batch(fs_plan* p) {
   b.col_grid = b.col_total;
   b.row_smem = rsm;
   b.col_smem = csm;
-  p->batch = true;
+  b.row_form = b.col_form = 1;  // until tuned
+  if (v2) {
+    b.maps2 = reinterpret_cast<const CUtensorMap*>(dev + o_m2);
+    b.row2_begin = reinterpret_cast<const long long*>(dev + o_rb2);
+    b.col2_begin = reinterpret_cast<const long long*>(dev + o_cb2);
+    b.col2_pairs = reinterpret_cast<const int*>(dev + o_p2);
+    b.row2_total = rb2[nm];
+    b.col2_total = cb2[nm];
+    b.row2_grid = b.row2_total;
+    b.col2_grid = b.col2_total;
+    b.row2_smem = rsm2;
+    b.col2_smem = csm2;
+  }
   return FS_OK;
 }
 
-// Autotuner of the batched launches: times the persistent grid sizes
-// {1, 2, 3, 4, 6, 8, 16} x SMs and one CTA per work item for each pass and
-// keeps the fastest.  Runs on the state just set (row pass from the real
-// fields, column pass on its output), which it leaves unchanged.
+// Autotuner of the batched launches.  For each pass it times every form the
+// ensemble supports -- the half-length row / column-tile kernels (radix-16
+// line transforms, column tiles of col_tk columns) and, for FP32 members with
+// both axes in [64, 1024], the warp-per-line kernels (radix-32 / 16 / 8 ...
+// line transforms held by one warp, two-column tiles) -- at the persistent
+// grid sizes {1, 2, 3, 4, 5, 6, 8, 16} x SMs and one CTA per work item, and
+// keeps the fastest (form, grid) pair.  Runs on the state just set (row pass
+// from the real fields, column pass on its output), which it leaves
+// unchanged.
 cudaError_t autotune_batch(fs_plan* p) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int mult[] = {1, 2, 3, 4, 6, 8, 16};
+  const int mult[] = {1, 2, 3, 4, 5, 6, 8, 16};
   cudaEvent_t e0, e1;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) return e;
+  fs::BatchArgs& b = p->bargs;
+  const bool v2 = b.maps2 != nullptr;
+  // the column pass is timed on the output of a row pass in the current row form
+  b.row_form = 1;
   for (int kind = 0; kind < 2 && e == cudaSuccess; ++kind) {
-    long long total = kind == 0 ? p->bargs.row_total : p->bargs.col_total;
-    std::vector<long long> cand;
-    for (int mm : mult)
-      if ((long long)mm * sms < total) cand.push_back((long long)mm * sms);
-    cand.push_back(total);
     float best = 1e30f;
-    long long best_g = total;
-    for (long long g : cand) {
-      if (kind == 0) p->bargs.row_grid = g; else p->bargs.col_grid = g;
-      float acc = 0.f;
-      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
-        if (kind == 1) e = launch_batch_pass(p, 1, 0, p->stream);  // fresh column input
-        if (e == cudaSuccess) e = cudaEventRecord(e0, p->stream);
-        if (e == cudaSuccess) e = launch_batch_pass(p, 1, kind, p->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float t = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-        if (rep > 0) acc += t;  // first repetition warms up
-      }
-      if (acc < best) {
-        best = acc;
-        best_g = g;
+    int best_form = 1;
+    long long best_g = 0;
+    const int pinned = kind == 0 ? p->row_form : p->col_form;  // fs_set_pass_forms, 0: free
+    for (int form = 1; form <= (v2 ? 2 : 1) && e == cudaSuccess; ++form) {
+      if (pinned && form != pinned) continue;
+      const long long total = kind == 0 ? (form == 2 ? b.row2_total : b.row_total)
+                                        : (form == 2 ? b.col2_total : b.col_total);
+      std::vector<long long> cand;
+      for (int mm : mult)
+        if ((long long)mm * sms < total) cand.push_back((long long)mm * sms);
+      cand.push_back(total);
+      for (long long g : cand) {
+        if (kind == 0) {
+          b.row_form = form;
+          (form == 2 ? b.row2_grid : b.row_grid) = g;
+        } else {
+          b.col_form = form;
+          (form == 2 ? b.col2_grid : b.col_grid) = g;
+        }
+        float acc = 0.f;
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+          if (kind == 1) e = launch_batch_pass(p, 1, 0, p->stream);  // fresh column input
+          if (e == cudaSuccess) e = cudaEventRecord(e0, p->stream);
+          if (e == cudaSuccess) e = launch_batch_pass(p, 1, kind, p->stream);
+          if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          float t = 0.f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+          if (rep > 0) acc += t;  // first repetition warms up
+        }
+        if (acc < best) {
+          best = acc;
+          best_form = form;
+          best_g = g;
+        }
       }
     }
-    if (kind == 0) p->bargs.row_grid = best_g; else p->bargs.col_grid = best_g;
+    if (kind == 0) {
+      b.row_form = best_form;
+      (best_form == 2 ? b.row2_grid : b.row_grid) = best_g;
+    } else {
+      b.col_form = best_form;
+      (best_form == 2 ? b.col2_grid : b.col_grid) = best_g;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1283,13 +1380,18 @@ fs_status fs_profile_read(fs_plan_t p, double* ms_per_pass, int64_t* launches_pe
 
 fs_status fs_set_pass_forms(fs_plan_t p, int row_form, int col_form) {
   if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
-  if (row_form < 0 || row_form > 2 || col_form < 0 || col_form > 2)
-    return fail(p, FS_ERR_INVALID_ARG, "pass forms are 0 (default), 1 (half-length / tile) or 2 (warp per line)");
+  if (row_form < 0 || row_form > 3 || col_form < 0 || col_form > 3)
+    return fail(p, FS_ERR_INVALID_ARG,
+                "pass forms are 0 (default), 1 (half-length / tile), 2 (warp per line), 3 (two warps per line)");
   const Member& m = p->members[0];
-  if ((row_form == 2 && !m.tw_row2) || (col_form == 2 && !m.tw_col2))
+  const bool r2ok = p->batch ? p->bargs.maps2 != nullptr : m.tw_row2 != nullptr;
+  const bool c2ok = p->batch ? p->bargs.maps2 != nullptr : m.tw_col2 != nullptr;
+  const bool r3ok = !p->batch && m.tw_row2w != nullptr, c3ok = !p->batch && m.tw_col2w != nullptr;
+  if ((row_form == 2 && !r2ok) || (col_form == 2 && !c2ok) || (row_form == 3 && !r3ok) || (col_form == 3 && !c3ok))
     return fail(p, FS_ERR_UNSUPPORTED, "the warp-per-line form does not cover this plan's grid or precision");
   p->row_form = row_form;
   p->col_form = col_form;
+  if (p->batch) p->tuned = false;  // the next fs_set_fields tunes again within the pinned forms
   drop_graph(p);  // the captured launches hold the arguments by value
   return FS_OK;
 }
@@ -1303,13 +1405,17 @@ fs_status fs_test_short_wait(fs_plan_t p, int enable) {
 }
 
 fs_status fs_batch_schedule(fs_plan_t p, int64_t* row_grid, int64_t* col_grid, int64_t* row_items,
-                            int64_t* col_items) {
+                            int64_t* col_items, int* row_form, int* col_form) {
   if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
   if (!p->batch) return fail(p, FS_ERR_INVALID_ARG, "not a batched plan");
-  if (row_grid) *row_grid = p->bargs.row_grid;
-  if (col_grid) *col_grid = p->bargs.col_grid;
-  if (row_items) *row_items = p->bargs.row_total;
-  if (col_items) *col_items = p->bargs.col_total;
+  const fs::BatchArgs& b = p->bargs;
+  const bool r2 = b.row_form == 2, c2 = b.col_form == 2;
+  if (row_grid) *row_grid = r2 ? b.row2_grid : b.row_grid;
+  if (col_grid) *col_grid = c2 ? b.col2_grid : b.col_grid;
+  if (row_items) *row_items = r2 ? b.row2_total : b.row_total;
+  if (col_items) *col_items = c2 ? b.col2_total : b.col_total;
+  if (row_form) *row_form = b.row_form;
+  if (col_form) *col_form = b.col_form;
   return FS_OK;
 }
 

@@ -73,7 +73,7 @@ def bind(path: str):
         "fs_step_profiled": [plan, ctypes.c_int64],
         "fs_profile_read": [plan, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                             ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
-        "fs_batch_schedule": [plan] + [ctypes.POINTER(ctypes.c_int64)] * 4,
+        "fs_batch_schedule": [plan] + [ctypes.POINTER(ctypes.c_int64)] * 4 + [ctypes.POINTER(ctypes.c_int)] * 2,
         "fs_workspace_bytes": [plan, ctypes.POINTER(ctypes.c_size_t)],
         "fs_last_launch_count": [plan, ctypes.POINTER(ctypes.c_int64)],
         "fs_destroy": [plan],
@@ -233,10 +233,12 @@ def fs_profile_read(plan, npass_max: int = 8):
 
 
 def fs_batch_schedule(plan):
-    """(row grid, column grid, row items, column items) of a batched plan."""
+    """(row grid, column grid, row items, column items, row form, column form)
+    of a batched plan, as chosen by the autotuner."""
     v = [ctypes.c_int64() for _ in range(4)]
-    _check(lib().fs_batch_schedule(plan, *[ctypes.byref(x) for x in v]), plan)
-    return tuple(x.value for x in v)
+    f = [ctypes.c_int() for _ in range(2)]
+    _check(lib().fs_batch_schedule(plan, *[ctypes.byref(x) for x in v + f]), plan)
+    return tuple(x.value for x in v + f)
 
 
 def fs_set_pass_forms(plan, row_form: int, col_form: int):

@@ -58,7 +58,7 @@ def test_fp64_batch_matches_oracle_per_member(F, O):
         r5, _ = O.step(pr, f0, 5)
         assert rel_linf(g1, r1) <= 1e-12
         assert rel_linf(g5, r5) <= 1e-11
-    row_grid, col_grid, row_items, col_items = sched
+    row_grid, col_grid, row_items, col_items, row_form, col_form = sched
     assert 0 < row_grid <= row_items and 0 < col_grid <= col_items
 
 
@@ -87,7 +87,32 @@ def test_batch_equals_single_plans(F):
         plan.step(40)
         ref = plan.get_fields().double().cpu().numpy()
         plan.close()
-        assert rel_linf(g, ref) <= 1e-5
+        # FP32 parity bound of 2e-6 per step, times 40 steps, times 2 (growth)
+        assert rel_linf(g, ref) <= 2e-6 * 40 * 2
+
+
+@pytest.mark.parametrize("forms", [(1, 1), (2, 2), (2, 1), (1, 2)])
+def test_fp32_batch_forms_match_oracle(F, O, forms):
+    """Both ensemble kernel forms, pinned per pass, against the oracle member
+    by member after one step and after 34 (the graph path)."""
+    import torch
+    probs = mixed_problems([(128, 128), (256, 256), (1024, 512), (512, 1024), (64, 128)], p=2, seed=4)
+    fields = [I.noise_fields(pr, seed=50 + i) for i, pr in enumerate(probs)]
+    plan = F.Plan(probs, "f32")
+    F.fs_set_pass_forms(plan.h, *forms)
+    plan.set_fields([torch.tensor(f, dtype=torch.float32, device="cuda") for f in fields])
+    sched = F.fs_batch_schedule(plan.h)
+    assert sched[4:] == forms
+    plan.step(1)
+    out1 = [o.double().cpu().numpy() for o in plan.get_fields()]
+    plan.step(33)
+    out34 = [o.double().cpu().numpy() for o in plan.get_fields()]
+    plan.close()
+    for pr, f0, g1, g34 in zip(probs, fields, out1, out34):
+        r1, _ = O.step(pr, f0, 1)
+        r34, _ = O.step(pr, r1, 33)
+        assert rel_linf(g1, r1) <= 2e-6 * 2, (pr.n, forms)
+        assert rel_linf(g34, r34) <= 2e-6 * 34 * 2, (pr.n, forms)
 
 
 def test_batch_rejects_unsupported_members(F):
