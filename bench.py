@@ -446,7 +446,8 @@ def extras(steps: int, warmup: int, device: int, peak, peak_kind):
                              "ms_per_step": r["total_ms"] / k, "dt": pr.dt, "launches": r["launches"],
                              "workspace_bytes": r["workspace_bytes"],
                              "roofline": roofline_entry(["fs_row_kernel", "fs_col_kernel"],
-                                                        [3 * nf4 * N * s] * 2, r, peak, peak_kind)}
+                                                        [3 * nf4 * N * s] * 2, r, peak, peak_kind,
+                                                        "traffic_2d_2048_p4.txt")}
     out["2d_2048_p4_f32"]["roofline"]["step"] = step_entry(6 * nf4 * N * s, 2 * nf4 * N * s,
                                                            r["total_ms"] / k, peak,
                                                            design_bytes=(4 * nf4 + 1) * N * s)

@@ -22,6 +22,9 @@ def main(argv=None):
     ap.add_argument("--dt-factor", type=float, default=6.0)
     ap.add_argument("--scheme", default="fs", choices=["fs", "fd"])
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--forms", type=int, nargs=2, default=None, metavar=("ROW", "COL"),
+                    help="kernel forms of the row and column passes (fs_set_pass_forms: 0 default, 1 half-length "
+                         "/ tile, 2 warp per line, 3 two warps per line)")
     args = ap.parse_args(argv)
 
     import torch
@@ -32,6 +35,8 @@ def main(argv=None):
     f0 = torch.tensor(I.noise_fields(pr, seed=args.seed), dtype=dtype, device="cuda")
     scheme = fs.FS_SCHEME_EXPLICIT_FD if args.scheme == "fd" else fs.FS_SCHEME_SEMI_IMPLICIT_FS
     plan = fs.Plan(pr, args.precision, scheme=scheme)
+    if args.forms:
+        fs.fs_set_pass_forms(plan.h, *args.forms)
     plan.set_fields(f0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
