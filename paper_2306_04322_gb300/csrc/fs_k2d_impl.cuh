@@ -77,6 +77,7 @@ cudaError_t col_launch_tc(const KArgs& a, const CUtensorMap& tm, cudaStream_t s)
   static unsigned done = 0;
   cudaError_t e = allow_big_smem(fs_col_kernel<T, NY, TCM>, &done);
   if (e != cudaSuccess) return e;
+  if (TCM == TC_TF32 && (tk * Cfg::TPL) % 128 != 0) return cudaErrorNotSupported;  // 128-row MMAs
   dim3 grid((unsigned)(a.nx / 2 / tk), (unsigned)a.nf);
   return launch_pdl(fs_col_kernel<T, NY, TCM>, grid, dim3((unsigned)(tk * Cfg::TPL)), smem, s, a, tm);
 }

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(LineCfg<T, NY>::THREADS, 4)
       float* bsm = reinterpret_cast<float*>(tile + Cfg::TROWS * tk);
       tc_load_b(bsm, reinterpret_cast<const float*>(a.tc_b));
       __syncthreads();
-      tc_first_pass16<NY, TCM>(reinterpret_cast<float2*>(tile), tk, bsm);
+      tc_first_pass16<NY, TCM>(reinterpret_cast<float2*>(tile), tk, bsm, a.flag);
 #pragma unroll
       for (int m = 0; m < E; ++m) v[m] = ld(t + TPL * m);
       stockham<NY, E, 16, DIR>(v, t, tw, st, ld, sync);
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(LineCfg<T, NZ>::THREADS, 4)
     auto st = [tl, tk](int q, C x) { tl[(q + (q >> LOGE)) * tk] = x; };
     auto ld = [tl, tk](int q) { return tl[(q + (q >> LOGE)) * tk]; };
     if constexpr (TCM != TC_NONE) {
-      tc_first_pass16<NZ, TCM>(reinterpret_cast<float2*>(tiles + i * TROWS * tk), tk, bsm);
+      tc_first_pass16<NZ, TCM>(reinterpret_cast<float2*>(tiles + i * TROWS * tk), tk, bsm, a.flag);
 #pragma unroll
       for (int m = 0; m < E; ++m) v[m] = ld(t + TPL * m);
       stockham<NZ, E, 16, -1>(v, t, tw, st, ld, sync);
@@ -322,7 +322,10 @@ template <typename T, int NY, int DIR, int TCM>
 cudaError_t ypass_launch_tc(const KArgs& a, const CUtensorMap& tm, int nslots, cudaStream_t s) {
   using Cfg = LineCfg<T, NY>;
   const int tk = line_tk<T, NY>(a.nx);
-  size_t smem = Cfg::HEAD + (size_t)Cfg::TROWS * tk * sizeof(cplx<T>) + (TCM ? 8192 : 0);
+  size_t smem = Cfg::HEAD + (size_t)Cfg::TROWS * tk * sizeof(cplx<T>) + (TCM ? 8192 : 0) +
+                (TCM == TC_TF32 ? tc5_extra_bytes(tk * Cfg::TPL) : 0);
+  // the tcgen05 stage runs 128-row MMAs over the CTA's (butterfly, column) rows
+  if (TCM == TC_TF32 && (tk * Cfg::TPL) % 128 != 0) return cudaErrorNotSupported;
   static unsigned done = 0;
   cudaError_t e = allow_big_smem(fs_ypass_kernel<T, NY, DIR, TCM>, &done);
   if (e != cudaSuccess) return e;
@@ -345,7 +348,9 @@ template <typename T, int NZ, int TCM>
 cudaError_t zstep_launch_tc(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
   using Cfg = LineCfg<T, NZ>;
   const int tk = line_tk<T, NZ>(a.nx);
-  size_t smem = Cfg::HEAD + 2 * (size_t)Cfg::TROWS * tk * sizeof(cplx<T>) + (TCM ? 8192 : 0);
+  size_t smem = Cfg::HEAD + 2 * (size_t)Cfg::TROWS * tk * sizeof(cplx<T>) + (TCM ? 8192 : 0) +
+                (TCM == TC_TF32 ? tc5_extra_bytes(tk * Cfg::TPL) : 0);
+  if (TCM == TC_TF32 && (tk * Cfg::TPL) % 128 != 0) return cudaErrorNotSupported;
   static unsigned done = 0;
   cudaError_t e = allow_big_smem(fs_zstep_kernel<T, NZ, TCM>, &done);
   if (e != cudaSuccess) return e;

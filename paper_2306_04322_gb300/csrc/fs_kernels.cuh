@@ -505,7 +505,8 @@ struct KUpdate {
 // (plus the split DFT matrix of the tensor-core stage).
 template <typename T, int NY, int TCM = TC_NONE>
 constexpr size_t col_smem_bytes(int tk) {
-  return ColCfg<T, NY>::HEAD + 2 * (size_t)ColCfg<T, NY>::TROWS * tk * sizeof(cplx<T>) + (TCM ? 8192 : 0);
+  return ColCfg<T, NY>::HEAD + 2 * (size_t)ColCfg<T, NY>::TROWS * tk * sizeof(cplx<T>) + (TCM ? 8192 : 0) +
+         (TCM == TC_TF32 ? tc5_extra_bytes(ColCfg<T, NY>::TPL * tk) : 0);
 }
 
 // One column-pass work item: kx tile bx, field group g of the simulation
@@ -580,7 +581,7 @@ __device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap
     if constexpr (TCM != TC_NONE) {
       if (!inv) {
         // first radix-16 pass on tensor cores, the rest on CUDA cores
-        tc_first_pass16<NY, TCM>(reinterpret_cast<float2*>(tiles + it * TROWS * tk), tk, bsm);
+        tc_first_pass16<NY, TCM>(reinterpret_cast<float2*>(tiles + it * TROWS * tk), tk, bsm, a.flag);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = ld(t + TPL * m);
         stockham<NY, E, 16, -1>(v, t, twc, st, ld, sync);

@@ -563,12 +563,15 @@ float split_hi(float x, int mode) {
 
 // B = [[Wr, Wi], [-Wi, Wr]] (32 x 32; row kc = input index r, +16 for the
 // imaginary half; column nc = output index k, +16 for the imaginary half),
-// W[r][k] = exp(-2 pi i r k / 16), split into hi and lo halves and stored in
-// the MMA fragment order the device reads with one 16-byte load per lane:
-//   TF32 (m16n8k8):  [nn < 4][kk < 4][lane][hi(k0, nc), hi(k0 + 4, nc), lo(k0, nc), lo(k0 + 4, nc)],
-//                    k0 = 8 kk + lane % 4, nc = 8 nn + lane / 4;
-//   BF16 (m16n8k16): [nn < 4][kk < 2][lane][hi pair(k0), hi pair(k0 + 8), lo pair(k0), lo pair(k0 + 8)],
-//                    k0 = 16 kk + 2 (lane % 4), pair(k) = bf16(B[k][nc]) | bf16(B[k + 1][nc]) << 16.
+// W[r][k] = exp(-2 pi i r k / 16), split into hi and lo halves:
+//   TF32 (tcgen05 kind::tf32): B_hi then B_lo, 1024 words each, in the
+//     canonical K-major layout without swizzle that the shared-memory
+//     descriptor describes: core matrices of 8 N-rows x 4 K-values (16
+//     bytes per row), word offset ((nc / 8) * 8 + kc / 4) * 32 + (nc % 8) * 4
+//     + kc % 4 (core matrices 128 bytes apart along K, 1024 along N);
+//   BF16 (mma.sync m16n8k16): fragment order, one 16-byte load per lane:
+//     [nn < 4][kk < 2][lane][hi pair(k0), hi pair(k0 + 8), lo pair(k0), lo pair(k0 + 8)],
+//     k0 = 16 kk + 2 (lane % 4), pair(k) = bf16(B[k][nc]) | bf16(B[k + 1][nc]) << 16.
 void tc_table(int mode, uint32_t* out) {
   const long double pi = 3.141592653589793238462643383279502884L;
   float hi[32][32], lo[32][32];
@@ -589,25 +592,26 @@ void tc_table(int mode, uint32_t* out) {
   auto pair = [&](const float (&m)[32][32], int k, int nc) {
     return (bits(m[k][nc]) >> 16) | (bits(m[k + 1][nc]) & 0xFFFF0000u);
   };
-  const int nkk = mode == kTcTf32 ? 4 : 2;
+  if (mode == kTcTf32) {
+    for (int nc = 0; nc < 32; ++nc)
+      for (int kc = 0; kc < 32; ++kc) {
+        const int w = ((nc / 8) * 8 + kc / 4) * 32 + (nc % 8) * 4 + kc % 4;
+        out[w] = bits(hi[kc][nc]);
+        out[1024 + w] = bits(lo[kc][nc]);
+      }
+    return;
+  }
+  const int nkk = 2;
   for (int nn = 0; nn < 4; ++nn)
     for (int kk = 0; kk < nkk; ++kk)
       for (int lane = 0; lane < 32; ++lane) {
         const int nc = 8 * nn + lane / 4, t4 = lane % 4;
         uint32_t* w = out + (((nn * nkk + kk) * 32 + lane) * 4);
-        if (mode == kTcTf32) {
-          const int k0 = 8 * kk + t4;
-          w[0] = bits(hi[k0][nc]);
-          w[1] = bits(hi[k0 + 4][nc]);
-          w[2] = bits(lo[k0][nc]);
-          w[3] = bits(lo[k0 + 4][nc]);
-        } else {
-          const int k0 = 16 * kk + 2 * t4;
-          w[0] = pair(hi, k0, nc);
-          w[1] = pair(hi, k0 + 8, nc);
-          w[2] = pair(lo, k0, nc);
-          w[3] = pair(lo, k0 + 8, nc);
-        }
+        const int k0 = 16 * kk + 2 * t4;
+        w[0] = pair(hi, k0, nc);
+        w[1] = pair(hi, k0 + 8, nc);
+        w[2] = pair(lo, k0, nc);
+        w[3] = pair(lo, k0 + 8, nc);
       }
 }
 
