@@ -17,7 +17,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2306_04322_gb300")
     ap.add_argument("--grid", type=int, nargs="+", default=[1024, 1024])
     ap.add_argument("--p", type=int, default=2)
-    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "tf32", "bf16x3"])
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--dt-factor", type=float, default=6.0)
     ap.add_argument("--scheme", default="fs", choices=["fs", "fd"])
