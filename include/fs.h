@@ -165,10 +165,11 @@ FS_API fs_status fs_set_params(fs_plan_t plan, const fs_params* prm);
 FS_API fs_status fs_set_stream(fs_plan_t plan, void* stream);
 
 /* Total free energy, Eq. (fe), of the current state (rectangle rule, dV =
- * prod dx, gradient terms through Parseval with the plan's |xi|^2).
- * parts (may be NULL) receives 2 + p values: chemical, c-gradient and each
- * eta_i-gradient contribution.  Synchronises.  Built for 2D
- * semi-implicit FS plans of one simulation; others return
+ * prod dx, gradient terms through Parseval with the plan's |xi|^2 of Eq.
+ * (Gamma_fft) / (Gamma_fft_3d) or the FS-FD forms).  parts (may be NULL)
+ * receives 2 + p values: chemical, c-gradient and each eta_i-gradient
+ * contribution.  Synchronises.  Built for semi-implicit FS plans of one
+ * simulation, 2D and 3D; batched and explicit-FD plans return
  * FS_ERR_UNSUPPORTED.  The spectra are overwritten: the next step starts
  * again from the real fields (as after fs_set_fields). */
 FS_API fs_status fs_free_energy(fs_plan_t plan, double* F, double* parts);

@@ -106,6 +106,10 @@ cudaError_t ypass_launch_f32(const KArgs& a, const CUtensorMap& tm, int dir, int
 cudaError_t ypass_launch_f64(const KArgs& a, const CUtensorMap& tm, int dir, int nslots, cudaStream_t s);
 cudaError_t zstep_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
 cudaError_t zstep_launch_f64(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
+// Free-energy diagnostic, 3D: z transforms and sums of w K2 |phi^|^2 after
+// the x pass in mode 3 and the forward y pass over slots 0..nf-1.
+cudaError_t energy_z_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
+cudaError_t energy_z_launch_f64(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
 int line_tile_width_f32(int nx, int nl);
 int line_tile_width_f64(int nx, int nl);
 // Batched ensemble launches (fs_batch_f32.cu / fs_batch_f64.cu).

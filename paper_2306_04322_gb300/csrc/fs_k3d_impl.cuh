@@ -318,6 +318,117 @@ int line_tk(int nx) {
   return LineCfg<T, NL>::TK < Lh ? LineCfg<T, NL>::TK : Lh;
 }
 
+// ---------------------------------------------------------------------------
+// Free-energy diagnostic, 3D gradient terms (Eq. fe through Parseval with the
+// scheme's |xi|^2 of Eq. Gamma_fft_3d, K2 = kx^2 + ky^2 + kz^2).  Input: the
+// x pass in mode 3 (2 x^(phi) of every field in slots 0..nf-1) and the
+// forward y pass over those slots (the kx = 0 / Nyquist column packed as
+// described at the top of this file).  One CTA per (kx tile, ky storage row,
+// field g): forward z transform of the z lines, then the sum of w K2 |.|^2
+// over the line, each stored mode weighted by the modes of the full spectrum
+// it stands for:
+//   kx >= 1: weight 2 (the conjugate mode at -k is not stored);
+//   packed column, rows 0 < ky < ny/2: x-DC modes (0, ky, kz), weight 2;
+//   rows ky > ny/2: x-Nyquist modes (nx/2, ny - ky, kz), weight 2;
+//   rows 0 and ny/2: P + i Q of two real z sequences (y-DC and y-Nyquist of
+//   the x-DC resp. x-Nyquist column), separated through Z(kz) and
+//   conj Z(-kz), each mode once (weight 1).
+// FP64 atomics into acc[1 + g].
+// ---------------------------------------------------------------------------
+template <typename T, int NZ>
+__global__ void __launch_bounds__(LineCfg<T, NZ>::THREADS, 4)
+    fs_energy_z_kernel(KArgs a, const __grid_constant__ CUtensorMap tmap) {
+  using C = cplx<T>;
+  using Cfg = LineCfg<T, NZ>;
+  constexpr int E = Cfg::E, TPL = Cfg::TPL, BH = Cfg::BH, LOGE = Cfg::LOGE;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  C* tw = reinterpret_cast<C*>(smem_raw + Cfg::BAR_BYTES);
+  T* k2zt = reinterpret_cast<T*>(smem_raw + Cfg::BAR_BYTES + Cfg::TW_BYTES);
+  C* tile = reinterpret_cast<C*>(smem_raw + Cfg::HEAD);
+  const int tk = blockDim.x / TPL;
+  const int j = threadIdx.x % tk, t = threadIdx.x / tk;
+  const int Lh = a.nx / 2, NY = a.ny;
+  const int kx0 = blockIdx.x * tk, kx = kx0 + j;
+  const int ky = blockIdx.y;  // storage row
+  const int g = blockIdx.z;   // field
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(bar, (uint32_t)(NZ * tk * sizeof(C)));
+    const int cx = kx0 * (int)(sizeof(C) / 8);
+    for (int z0 = 0; z0 < NZ; z0 += BH) tma_load_4d(tile + z0 * tk, &tmap, cx, ky, z0, g, bar);
+  }
+  copy_to_smem(tw, reinterpret_cast<const C*>(a.tw_z), Cfg::TWS);
+  for (int i = threadIdx.x; i < NZ; i += blockDim.x) k2zt[i] = reinterpret_cast<const T*>(a.k2z)[i];
+  __syncthreads();
+  if (!mbar_wait_bounded(bar, 0, first_wait_polls(a))) {
+    if (threadIdx.x == 0) atomicOr(a.flag, FS_FLAG_TIMEOUT);
+    mbar_wait_bounded(bar, 0, kWaitPolls);
+    return;
+  }
+  C v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = tile[(t + TPL * m) * tk + j];
+  {
+    C* tl = tile + j;
+    auto st = [tl, tk](int q, C x) { tl[(q + (q >> LOGE)) * tk] = x; };
+    auto ld = [tl, tk](int q) { return tl[(q + (q >> LOGE)) * tk]; };
+    line_fft<NZ, E, -1>(v, t, tw, st, ld, []() { __syncthreads(); });
+  }
+  const T* __restrict__ k2xt = reinterpret_cast<const T*>(a.k2x);
+  const T* __restrict__ k2yt = reinterpret_cast<const T*>(a.k2y);
+  const bool col0 = (kx0 == 0 && j == 0);
+  const bool pairCTA = (kx0 == 0) && (ky == 0 || ky == NY / 2);  // CTA-uniform
+  const bool pair = pairCTA && j == 0;
+  if (pairCTA) {
+    // the pair rows need Z(-kz): the transformed line in natural order
+    __syncthreads();
+    if (j == 0) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) tile[(t + TPL * m) * tk] = v[m];
+    }
+    __syncthreads();
+  }
+  // K2 without the z part, and the weight, of a line that holds one mode set
+  const double kxy = (double)(col0 ? (ky <= NY / 2 ? k2xt[0] : k2xt[Lh]) : k2xt[kx]) + (double)k2yt[ky];
+  const double kxa = (double)((ky == 0) ? k2xt[0] : k2xt[Lh]);  // pair rows: x part of both modes
+  const double kya = (double)k2yt[0], kyb = (double)k2yt[NY / 2];
+  double sum = 0.0;
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int kz = t + TPL * m;
+    const double kz2 = (double)k2zt[kz];
+    if (pair) {
+      const C pz = cconj(tile[((NZ - kz) & (NZ - 1)) * tk]);
+      const C P = cscale(cadd(v[m], pz), T(0.5)), Q = cscale(mul_i<-1>(csub(v[m], pz)), T(0.5));
+      sum += (kxa + kya + kz2) * ((double)P.x * P.x + (double)P.y * P.y);
+      sum += (kxa + kyb + kz2) * ((double)Q.x * Q.x + (double)Q.y * Q.y);
+    } else {
+      sum += 2.0 * (kxy + kz2) * ((double)v[m].x * v[m].x + (double)v[m].y * v[m].y);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&a.acc[1 + g], sum);
+}
+
+template <typename T, int NZ>
+cudaError_t energy_z_launch_n(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+  using Cfg = LineCfg<T, NZ>;
+  const int tk = line_tk<T, NZ>(a.nx);
+  const size_t smem = Cfg::HEAD + (size_t)Cfg::TROWS * tk * sizeof(cplx<T>);
+  static unsigned done = 0;
+  cudaError_t e = allow_big_smem(fs_energy_z_kernel<T, NZ>, &done);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)(a.nx / 2 / tk), (unsigned)a.ny, (unsigned)a.nf);
+  fs_energy_z_kernel<T, NZ><<<grid, (unsigned)(tk * Cfg::TPL), smem, s>>>(a, tm);
+  return cudaGetLastError();
+}
+
 template <typename T, int NY, int DIR, int TCM>
 cudaError_t ypass_launch_tc(const KArgs& a, const CUtensorMap& tm, int nslots, cudaStream_t s) {
   using Cfg = LineCfg<T, NY>;
@@ -389,6 +500,17 @@ cudaError_t zstep_launch_t(const KArgs& a, const CUtensorMap& tm, cudaStream_t s
   switch (a.nz) {
 #define FS_CASE(n) \
   case n: return zstep_launch_n<T, n>(a, tm, s);
+    FS_LINE_SIZES(FS_CASE)
+#undef FS_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t energy_z_launch_t(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+  switch (a.nz) {
+#define FS_CASE(n) \
+  case n: return energy_z_launch_n<T, n>(a, tm, s);
     FS_LINE_SIZES(FS_CASE)
 #undef FS_CASE
     default: return cudaErrorInvalidValue;

@@ -1196,8 +1196,8 @@ fs_status fs_free_energy(fs_plan_t p, double* F, double* parts) {
   if (!F) return fail(p, FS_ERR_INVALID_ARG, "F is NULL");
   if (p->state == kStateNone) return fail(p, FS_ERR_STATE, "fs_free_energy before fs_set_fields");
   const Member& m = p->members[0];
-  if (p->members.size() != 1 || p->fd || m.prm.ndim != 2)
-    return fail(p, FS_ERR_UNSUPPORTED, "fs_free_energy is built for single 2D semi-implicit FS plans");
+  if (p->members.size() != 1 || p->fd)
+    return fail(p, FS_ERR_UNSUPPORTED, "fs_free_energy is built for single semi-implicit FS plans");
   cudaError_t e = cudaSuccess;
   if (p->state == kStateSpec) {
     e = launch_row(p, make_args(p, m, 2), p->stream);
@@ -1207,9 +1207,21 @@ fs_status fs_free_energy(fs_plan_t p, double* F, double* parts) {
   const int nparts = 2 + m.prm.p;
   e = cudaMemsetAsync(p->acc, 0, sizeof(double) * nparts, p->stream);
   fs::KArgs a = make_args(p, m, 3);
-  if (e == cudaSuccess) e = launch_row(p, a, p->stream);
-  if (e == cudaSuccess)
-    e = p->f64 ? fs::energy_col_launch_f64(a, m.tmap_col, p->stream) : fs::energy_col_launch_f32(a, m.tmap_col, p->stream);
+  if (e == cudaSuccess) e = launch_row(p, a, p->stream);  // chemical sum, 2 x^(phi) of every field
+  if (m.prm.ndim == 2) {
+    if (e == cudaSuccess)
+      e = p->f64 ? fs::energy_col_launch_f64(a, m.tmap_col, p->stream)
+                 : fs::energy_col_launch_f32(a, m.tmap_col, p->stream);
+  } else {
+    // 3D: forward y of slots 0..nf-1 (column packing), then z and the weighted sums
+    fs::KArgs b = a;
+    b.plane0 = 0;
+    if (e == cudaSuccess)
+      e = p->f64 ? fs::ypass_launch_f64(b, m.tmap_col, -1, p->nf, p->stream)
+                 : fs::ypass_launch_f32(b, m.tmap_col, -1, p->nf, p->stream);
+    if (e == cudaSuccess)
+      e = p->f64 ? fs::energy_z_launch_f64(a, m.tmap_z, p->stream) : fs::energy_z_launch_f32(a, m.tmap_z, p->stream);
+  }
   double h[8] = {0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, p->acc, sizeof(double) * nparts, cudaMemcpyDeviceToHost, p->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);

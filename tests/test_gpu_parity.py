@@ -264,3 +264,34 @@ def test_free_energy_matches_oracle(F, O, precision, n, p, tol):
     plan.close()
     ref, _ = O.step(pr, g, 5)
     assert rel_linf(h, ref) <= (1e-12 if precision == "f64" else 2e-5)
+
+
+@pytest.mark.parametrize("precision,n,dx,p,tol", [
+    ("f64", (16, 32, 8), (1.0, 0.5, 2.0), 2, 1e-12), ("f64", (32, 16, 64), (0.7, 1.0, 1.3), 1, 1e-12),
+    ("f64", (8, 8, 8), (1.0, 1.0, 1.0), 3, 1e-12), ("f32", (64, 64, 64), (1.0, 1.0, 1.0), 2, 1e-5)])
+def test_free_energy_3d_matches_oracle(F, O, precision, n, dx, p, tol):
+    """Eq. (fe) with the 3D frequency vector (Eq. Gamma_fft_3d): the x pass's
+    chemical sum, then y and z transforms with the packed kx = 0 / Nyquist
+    column weighted mode by mode; against the oracle before and after steps."""
+    import torch
+    pr = I.Problem(n=n, dx=dx, p=p)
+    pr.dt = 5.0 * I.fd_stable_dt(pr)
+    f0 = I.noise_fields(pr, seed=15, amp=0.1)
+    dt = torch.float64 if precision == "f64" else torch.float32
+    plan = F.Plan(pr, precision)
+    plan.set_fields(torch.tensor(f0, dtype=dt, device="cuda"))
+    E0, parts0 = plan.free_energy()
+    f_in = f0.astype(np.float32).astype(np.float64) if precision == "f32" else f0
+    Fo, po = O.free_energy(pr, f_in, parts=True)
+    assert abs(E0 - Fo) <= tol * abs(Fo)
+    assert np.allclose(parts0, po, rtol=tol * 10, atol=tol * abs(Fo))
+    plan.step(6)
+    E1, _ = plan.free_energy()
+    g = plan.get_fields().double().cpu().numpy()
+    assert abs(E1 - O.free_energy(pr, g)) <= tol * abs(Fo)
+    assert E1 < E0
+    plan.step(3)
+    h = plan.get_fields().double().cpu().numpy()
+    plan.close()
+    ref, _ = O.step(pr, g, 3)
+    assert rel_linf(h, ref) <= (1e-12 if precision == "f64" else 2e-5)
