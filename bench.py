@@ -15,6 +15,9 @@ Output: one JSON line on rank 0 (see the keys at the end of main()).
 Multi-GPU (torchrun): every rank runs an independent replica (the step has no
 exchange between simulations); value = all ranks' grid-point-steps / the
 slowest rank's time.
+  --slab instead decomposes ONE grid (--slab-n^2, c + 2 eta, FP32) over the
+  ranks (include/fs_slab.h; NCCL point-to-point transposes): strong scaling,
+  value = the grid's points x steps / the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -47,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the 3D and ensemble measurements")
+    ap.add_argument("--slab", action="store_true", help="one grid decomposed over the ranks (strong scaling)")
+    ap.add_argument("--slab-n", type=int, default=1024, help="grid side of --slab")
     return ap.parse_args()
 
 
@@ -617,11 +622,77 @@ def job_value(world: int, npts: int, steps: int, slowest_seconds: float) -> floa
     return world * npts * steps / slowest_seconds
 
 
+def slab_bench(args):
+    """One grid decomposed over the ranks: every timed step is the row pass,
+    the forward transpose (NCCL point-to-point), the column pass and the back
+    transpose on every rank; L2 flushed (512 MB write) before every step,
+    outside the timed events."""
+    import socket
+    import torch
+    import torch.distributed as dist
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    else:
+        with socket.socket() as so:
+            so.bind(("127.0.0.1", 0))
+            port = so.getsockname()[1]
+        dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    from paper_2306_04322_gb300 import build as B
+    from paper_2306_04322_gb300 import fs
+    from paper_2306_04322_gb300 import inputs as I
+    from paper_2306_04322_gb300 import slab as S
+    B.build()
+    fs.lib()
+    pr = I.Problem(n=(args.slab_n, args.slab_n), p=P)
+    pr.dt = 6.0 * I.fd_stable_dt(pr)
+    d = S.DistributedSlab(pr, "f32")
+    f0 = I.noise_fields(pr, seed=0)
+    d.set_fields(torch.tensor(f0[:, d.layout.row_range()], dtype=torch.float32, device="cuda"))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    d.step(args.warmup)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for e0, e1 in ev:
+            flush.fill_(1.0)
+            e0.record()
+            d.step(1)
+            e1.record()
+        torch.cuda.synchronize()
+    d.sync()
+    dist.barrier()
+    t = reduce_max(sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3, dist, f"cuda:{local}")
+    npts = pr.n[0] * pr.n[1]
+    fwd, back = d.layout.exchange_bytes(8)
+    d.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": npts * args.steps / t, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"2D periodic {pr.n[0]}x{pr.n[1]}, c + 2 eta, FP32, dt = 6 x FD-stable dt, "
+                                   "seeded +-0.01 noise, one grid decomposed into slabs",
+                       "grid": list(pr.n), "p": P, "parallelism": f"slab{world}",
+                       "l2": "flushed (512 MB write) before every timed step"},
+            "exchange": {"bytes_per_rank_per_step": fwd + back, "forward": fwd, "back": back},
+            "gpu_launches": 4 * args.steps,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def main():
     args = parse()
     world, rank, local = dist_info()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.slab:
+        slab_bench(args)
         return
     import torch
     torch.cuda.set_device(local)

@@ -48,6 +48,9 @@ struct KArgs {
   long long slot_stride;   // complex values per spectrum slot
   long long npts;          // real points per field
   int nx, ny, nz, nf;
+  int nx_full;             // x points of the whole grid (nx, except for the column plan of a slab, whose
+                           // nx covers only its kx columns)
+  int kx_base;             // global kx of the plan's column 0 (0, except for a slab's column plan)
   long long lines;         // rows handled by a row pass (ny * nz)
   int mode;                // row pass: 0 step from spectra, 1 step from real, 2 inverse only
   int tc;                  // FP32 column transforms: 0 CUDA cores, 1 TF32 x 3, 2 BF16 x 3 tensor-core stage

@@ -401,7 +401,7 @@ __device__ __forceinline__ bool col2_body(const KArgs& a, const CUtensorMap* tma
   auto st = [xa](int q, C x) { xa[pad32(q)] = x; };
   auto ld = [xa](int q) { return xa[pad32(q)]; };
   const KUpdate<float> up(a);
-  const bool special = (kx0 == 0 && j == 0);  // the packed kx = 0 / Nyquist column
+  const bool special = (a.kx_base + kx0 == 0 && j == 0);  // the packed kx = 0 / Nyquist column
   const C* fz = regions + j * PL;             // df/dc^ of this column (region 0 of group 0)
 
   // One FFT call site: it 0 forward (all warps), it 1 inverse (c, eta) as

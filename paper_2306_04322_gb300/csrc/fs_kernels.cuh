@@ -482,7 +482,7 @@ struct KUpdate {
     // coefficients (powers of two, so exact).  3D steady state: c comes
     // straight from the previous z step, without the y inverse / forward
     // round trip that would multiply it by ny: fold that in too.
-    const T q = (a.carry3 && a.mode == 0) ? T(2 * a.nx) * T(a.ny) : T(2 * a.nx);
+    const T q = (a.carry3 && a.mode == 0) ? T(2 * a.nx_full) * T(a.ny) : T(2 * a.nx_full);
     Mdt_c = Mdt / q;
     scale_c = scale * q;
   }
@@ -555,7 +555,7 @@ __device__ __forceinline__ bool col_body(const KArgs& a, const CUtensorMap* tmap
   }
 
   const KUpdate<T> up(a);
-  const bool special = (kx0 == 0);  // CTA holding the packed DC/Nyquist column
+  const bool special = (a.kx_base + kx0 == 0);  // CTA holding the packed DC/Nyquist column
   const T kx2 = k2xt[kx];
   const T kxn2 = k2xt[Lh];  // Nyquist column
   C* stash = tiles;  // c group: transformed df/dc, natural layout [ky][j]

@@ -14,6 +14,7 @@
 #include "fs.h"
 #include "fs_fft.cuh"
 #include "fs_internal.h"
+#include "fs_slab_hooks.h"
 
 namespace {
 
@@ -45,6 +46,11 @@ struct Member {
   void* tw_col2w = nullptr;
   double* csum = nullptr;
   long long slot_stride = 0;
+  // column plan of a slab (fs_slab_*): its nx covers kx columns kx_base ..
+  // kx_base + nx/2 - 1 of a grid of nx_full x points and npts_full points
+  // (0: an ordinary plan)
+  int kx_base = 0, nx_full = 0;
+  long long npts_full = 0;
   CUtensorMap tmap_col;  // [slot * nz + z][y][kx] tiles of the 2D column pass / 3D y passes
   CUtensorMap tmap_z;    // [slot][z][y][kx] z lines of the 3D z step
   CUtensorMap tmap_col2; // [slot][y][kx] two-column tiles of the warp-per-column pass
@@ -272,6 +278,8 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   a.slot_stride = m.slot_stride;
   a.npts = m.npts;
   a.nx = m.prm.n[0];
+  a.nx_full = m.nx_full ? m.nx_full : m.prm.n[0];
+  a.kx_base = m.kx_base;
   a.ny = m.prm.n[1];
   a.nz = m.prm.ndim > 2 ? m.prm.n[2] : 1;
   a.nf = p->nf;
@@ -290,8 +298,9 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   a.w = m.prm.w;
   a.alpha = m.prm.alpha;
   a.dt = m.prm.dt;
-  a.scale = 1.0 / (2.0 * (double)m.npts);
-  a.inv_npts = 1.0 / (double)m.npts;
+  const double ntot = (double)(m.npts_full ? m.npts_full : m.npts);
+  a.scale = 1.0 / (2.0 * ntot);
+  a.inv_npts = 1.0 / ntot;
   a.csum = p->f64 ? nullptr : m.csum;
   a.flag = p->flag;
   a.acc = p->acc;
@@ -1466,3 +1475,41 @@ const char* fs_last_error(fs_plan_t p) { return p ? p->err.c_str() : g_thread_er
 const char* fs_version(void) { return "fs-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---- hooks of the slab decomposition (fs_slab.cu) ---------------------------
+namespace fs {
+
+// Turn a single plan over nx' = 2 cols x points into the column plan of a
+// slab: its kx columns are kx_base .. kx_base + cols - 1 of the global grid
+// g (the k2x table gets their global |xi_x|^2, entry cols the global Nyquist
+// one), its update uses the global nx and N (scale 1/(2N), the carried c
+// scaling 2 nx), and only the slab holding kx_base = 0 separates the packed
+// kx = 0 / Nyquist column.
+cudaError_t slab_adopt_columns(fs_plan* p, int kx_base, const fs_params& g) {
+  Member& m = p->members[0];
+  const int cols = m.prm.n[0] / 2, nx = g.n[0];
+  m.kx_base = kx_base;
+  m.nx_full = nx;
+  m.npts_full = (long long)g.n[0] * g.n[1];
+  std::vector<double> k2(cols + 1);
+  for (int j = 0; j < cols; ++j) k2[j] = axis_k2(g.lap, kx_base + j, nx, g.dx[0]);
+  k2[cols] = axis_k2(g.lap, nx / 2, nx, g.dx[0]);
+  if (p->f64) return cudaMemcpy(m.k2x, k2.data(), sizeof(double) * k2.size(), cudaMemcpyHostToDevice);
+  std::vector<float> f(k2.begin(), k2.end());
+  return cudaMemcpy(m.k2x, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice);
+}
+
+// One pass of a single plan on its stream: kind 0 the row pass in `mode`
+// (0 from spectra, 1 from real fields, 2 inverse only), kind 1 the column pass.
+cudaError_t slab_pass(fs_plan* p, int kind, int mode) {
+  const Member& m = p->members[0];
+  const KArgs a = make_args(p, m, mode);
+  return kind == 0 ? launch_row(p, a, p->stream) : launch_col(p, m, a, p->stream);
+}
+
+void* slab_spec(fs_plan* p) { return p->members[0].spec; }
+void* slab_real(fs_plan* p) { return p->members[0].real; }
+double* slab_csum(fs_plan* p) { return p->members[0].csum; }
+fs_status slab_read_flag(fs_plan* p) { return read_flag(p); }
+
+}  // namespace fs

@@ -176,6 +176,7 @@ fs_status run_static(const fs_params& q, void* fields, int64_t nsteps, cudaStrea
   a.slot_stride = N / 2;
   a.npts = N;
   a.nx = nx;
+  a.nx_full = nx;
   a.ny = ny;
   a.nz = 1;
   a.nf = nf;

@@ -1,4 +1,5 @@
-"""Python binding of the C ABI in include/fs.h (ctypes; argument marshalling only).
+"""Python binding of the C ABI in include/fs.h and include/fs_slab.h (ctypes;
+argument marshalling only).
 
 The module-level functions carry the C names (fs_plan_create, fs_set_fields,
 fs_step, fs_get_fields, fs_destroy, ...) and take torch tensors or raw
@@ -39,6 +40,13 @@ class fs_params(ctypes.Structure):
                 ("rho2", ctypes.c_double), ("c_alpha", ctypes.c_double), ("c_beta", ctypes.c_double),
                 ("w", ctypes.c_double), ("alpha", ctypes.c_double), ("dt", ctypes.c_double),
                 ("precision", ctypes.c_int), ("lap", ctypes.c_int), ("scheme", ctypes.c_int)]
+
+
+class fs_slab_info(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int), ("nranks", ctypes.c_int), ("rows", ctypes.c_int), ("cols", ctypes.c_int),
+                ("slots_fwd", ctypes.c_int), ("slots_back", ctypes.c_int), ("elem_bytes", ctypes.c_size_t),
+                ("block_elems", ctypes.c_size_t), ("send", ctypes.c_void_p), ("recv", ctypes.c_void_p),
+                ("colspec", ctypes.c_void_p)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -82,6 +90,15 @@ def bind(path: str):
         "fs_set_pass_forms": [plan, ctypes.c_int, ctypes.c_int],
         "fs_measure_fp64_rate": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_double)],
+        "fs_slab_create": [P, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
+        "fs_slab_info_get": [ctypes.c_void_p, ctypes.POINTER(fs_slab_info)],
+        "fs_slab_set_fields": [ctypes.c_void_p, _vpp, ctypes.POINTER(ctypes.c_double)],
+        "fs_slab_set_c_sum": [ctypes.c_void_p, ctypes.c_double],
+        "fs_slab_row_pass": [ctypes.c_void_p],
+        "fs_slab_col_pass": [ctypes.c_void_p],
+        "fs_slab_get_fields": [ctypes.c_void_p, _vpp],
+        "fs_slab_sync": [ctypes.c_void_p],
+        "fs_slab_destroy": [ctypes.c_void_p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -89,6 +106,8 @@ def bind(path: str):
         f.restype = ctypes.c_int
     L.fs_last_error.argtypes = [plan]
     L.fs_last_error.restype = ctypes.c_char_p
+    L.fs_slab_last_error.argtypes = [ctypes.c_void_p]
+    L.fs_slab_last_error.restype = ctypes.c_char_p
     L.fs_version.argtypes = []
     L.fs_version.restype = ctypes.c_char_p
     return L
@@ -280,6 +299,60 @@ def fs_step2d_static(params: fs_params, fields, nsteps: int, stream=None) -> int
     returns the status code (no exception, the call sets no error text)."""
     s = _current_stream() if stream is None else ctypes.c_void_p(stream)
     return lib().fs_step2d_static(ctypes.byref(params), ctypes.c_void_p(_ptr(fields)), int(nsteps), s)
+
+
+# ---- slab decomposition (include/fs_slab.h) -----------------------------------
+
+def _check_slab(status: int, slab=None):
+    if status != FS_OK:
+        msg = lib().fs_slab_last_error(slab)
+        raise FSError(status, msg.decode() if msg else "")
+
+
+def fs_slab_create(params: fs_params, rank: int, nranks: int, stream=None):
+    h = ctypes.c_void_p()
+    s = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    _check_slab(lib().fs_slab_create(ctypes.byref(params), int(rank), int(nranks), s, ctypes.byref(h)))
+    return h
+
+
+def fs_slab_info_get(slab) -> fs_slab_info:
+    info = fs_slab_info()
+    _check_slab(lib().fs_slab_info_get(slab, ctypes.byref(info)), slab)
+    return info
+
+
+def fs_slab_set_fields(slab, fields) -> float:
+    """Returns the FP64 sum of this rank's c values."""
+    arr, keep = _ptr_array(fields)
+    total = ctypes.c_double()
+    _check_slab(lib().fs_slab_set_fields(slab, arr, ctypes.byref(total)), slab)
+    return total.value
+
+
+def fs_slab_set_c_sum(slab, c_sum_total: float):
+    _check_slab(lib().fs_slab_set_c_sum(slab, float(c_sum_total)), slab)
+
+
+def fs_slab_row_pass(slab):
+    _check_slab(lib().fs_slab_row_pass(slab), slab)
+
+
+def fs_slab_col_pass(slab):
+    _check_slab(lib().fs_slab_col_pass(slab), slab)
+
+
+def fs_slab_get_fields(slab, out):
+    arr, keep = _ptr_array(out)
+    _check_slab(lib().fs_slab_get_fields(slab, arr), slab)
+
+
+def fs_slab_sync(slab):
+    _check_slab(lib().fs_slab_sync(slab), slab)
+
+
+def fs_slab_destroy(slab):
+    _check_slab(lib().fs_slab_destroy(slab))
 
 
 def fs_version() -> str:
