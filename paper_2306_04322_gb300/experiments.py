@@ -4,6 +4,8 @@
     python -m paper_2306_04322_gb300.experiments accuracy    [--steps 10000]
     python -m paper_2306_04322_gb300.experiments cost        [--steps 200]
     python -m paper_2306_04322_gb300.experiments table1      [--t-span 1]
+    python -m paper_2306_04322_gb300.experiments table2      [--t-span 0.5]
+    python -m paper_2306_04322_gb300.experiments slab        [--steps 20]
 
 precision and accuracy start from the benchmark initial condition of
 Section 3 (Eqs. ic_c, ic_eta with p = 2, dx = 1), made periodic as the paper
@@ -26,6 +28,16 @@ cost: device time per step of the FS step and of the explicit FD scheme on
 table1: the paper's 2D accuracy study (Table 1 grids and time steps,
     domain 200, p = 4, E_phi against spectral FS FP64 on 2048^2 at
     dt = 1e-4) over t = 1 -> 1 + t_span; see table1_study.
+table2: the paper's 3D cases (Table 2 grids 16^3 .. 256^3 on the 100^3
+    domain, FS at dt = 5e-3, explicit FD at the paper's dt, p = 4, the 3D
+    initial condition of Eq. ic_eta_3d) over t = 1 -> 1 + t_span: device
+    time per unit of t and per step and point (the quantities of the
+    paper's 3D performance figure), and E_phi against spectral FS FP64 on
+    256^3 at a finer dt; see table2_study.
+slab: the slab decomposition (include/fs_slab.h) of 2D 1024^2 and 2048^2,
+    p = 2, FP32, over R = 1, 2, 4, 8 ranks held by one process: per-rank
+    device time of the row pass (with its transposes) and of the column
+    pass per step, against the single plan's step; see slab_study.
 """
 from __future__ import annotations
 
@@ -198,7 +210,7 @@ def spectral_resample(f: np.ndarray, n: int) -> np.ndarray:
 
 def table1_study(t_span: float = 1.0, grids=TABLE1_GRIDS, dts=TABLE1_FS_DTS, ref_dt: float = 1e-4,
                  pre_n: int = 512, l: float = 200.0, p: int = 4, precision: str = "f64", fd_dts=None,
-                 fd_max_steps: int = 100_000):
+                 fd_max_steps: int = 100_000, fsfd_ref_dt_max_grid: int | None = None):
     """The 2D accuracy study of Section 3 (Table 1, Eq. error_field) over a
     shortened time window.
 
@@ -214,7 +226,9 @@ def table1_study(t_span: float = 1.0, grids=TABLE1_GRIDS, dts=TABLE1_FS_DTS, ref
     E_eta (eta = sum_i eta_i) of Eq. error_field are taken at the points of
     each grid (the reference sampled every finest/n points).  `f32_floor`:
     the reference case run in FP32 against the FP64 reference, the error
-    FP32 rounding alone leaves after the dynamics amplify it."""
+    FP32 rounding alone leaves after the dynamics amplify it.  The FS-FD
+    forms at ref_dt run only on grids up to fsfd_ref_dt_max_grid (None: all;
+    on the finest grid they cost as much as the reference each)."""
     import torch
     from . import fs, inputs as I
     nmax = max(grids)
@@ -249,6 +263,8 @@ def table1_study(t_span: float = 1.0, grids=TABLE1_GRIDS, dts=TABLE1_FS_DTS, ref
         for lap, name in ((0, "FS"), (1, "FSFD2"), (2, "FSFD4")):
             for dt in dts:
                 steps = int(round(t_span / dt))
+                if lap and dt == ref_dt and fsfd_ref_dt_max_grid is not None and n > fsfd_ref_dt_max_grid:
+                    continue
                 if n == nmax and lap == 0 and dt == ref_dt and precision == "f64":
                     g, ms = ref, ms_ref
                 else:
@@ -269,11 +285,153 @@ def table1_study(t_span: float = 1.0, grids=TABLE1_GRIDS, dts=TABLE1_FS_DTS, ref
             "f32_floor": floor, "rows": rows}
 
 
+# Table 2 of the paper: grids and explicit FD time steps of the 3D cases
+# (FS at 5e-3 on every grid).
+TABLE2_GRIDS = (16, 32, 64, 128, 256)
+TABLE2_FD_DT = {16: 4.06e-2, 32: 2.54e-2, 64: 3.17e-3, 128: 7.94e-5, 256: 9.93e-6}
+
+
+def table2_study(t_span: float = 0.5, grids=TABLE2_GRIDS, fs_dt: float = 5e-3, ref_dt: float = 5e-4,
+                 pre_n: int = 512, l2d: float = 200.0, l3d: float = 100.0, p: int = 4, fd_dts=None,
+                 fd_f64_max_steps: int = 10_000, fd_max_steps: int = 60_000):
+    """The 3D cases of Section 3 (Table 2) over a shortened time window.
+
+    Setting of the paper: the 2D benchmark state at t = 1 (domain 200 x
+    200, p = 4, made periodic by explicit FD as in table1_study) placed on
+    the z = lz/2 plane of a cube of side lz = 100 with the (2x, 2y) scaling
+    (the n^2 grid of the 200-wide domain, index by index) and extruded along
+    z by Eq. ic_eta_3d, c = c0 (inputs.extrude_3d); every grid of Table 2
+    gets its own resampled state.  Runs t = 1 -> 1 + t_span: FS (spectral
+    |xi|^2 and the FS-FD O(dl^2) / O(dl^4) forms) at fs_dt, FP64, and
+    explicit FD at the paper's dt (FP64 up to fd_f64_max_steps steps, else
+    FP32 up to fd_max_steps).  Timing: device time of each run, per unit of
+    t and per step and point (the paper's 3D performance figure plots the
+    wall time of t = 1 -> 100 and the time per step and point).  Accuracy:
+    the paper compares none in 3D (its 256^3 grid is not fine enough for a
+    reference); here E_phi of Eq. error_field against spectral FS FP64 on
+    the finest grid at ref_dt < fs_dt, at the points of each grid -- a
+    measure of each grid and scheme against the best run this sweep has, not
+    against the continuum solution."""
+    import torch
+    from . import fs, inputs as I
+    nmax = max(grids)
+    pre = I.Problem(n=(pre_n, pre_n), dx=(l2d / pre_n, l2d / pre_n), p=p)
+    s_pre = periodic_benchmark_state(fs, pre).cpu().numpy()
+
+    def problem(n, dt, lap=0):
+        h = l3d / n
+        return I.Problem(n=(n, n, n), dx=(h, h, h), p=p, dt=dt, lap=lap)
+
+    def start(n, dtype=torch.float64):
+        f3 = I.extrude_3d(spectral_resample(s_pre, n), n, dz=l3d / n)
+        return torch.tensor(f3, dtype=dtype, device="cuda")
+
+    ref_steps = int(round(t_span / ref_dt))
+    ref, ms_ref = _run(fs, problem(nmax, ref_dt), start(nmax), ref_steps, "f64")
+    ref = ref.cpu()
+
+    def errs(n, g):
+        s = nmax // n
+        r = ref[:, ::s, ::s, ::s]
+        g = g.cpu()
+        return {"E_c": error_field(r[0], g[0]), "E_eta": error_field(r[1:].sum(0), g[1:].sum(0))}
+
+    rows = []
+    for n in grids:
+        npts = n ** 3
+        f0 = start(n)
+        steps = int(round(t_span / fs_dt))
+        for lap, name in ((0, "FS"), (1, "FSFD2"), (2, "FSFD4")):
+            g, ms = _run(fs, problem(n, fs_dt, lap), f0, steps, "f64")
+            rows.append({"grid": n, "scheme": name, "precision": "f64", "dt": fs_dt, "steps": steps, "ms": ms,
+                         "ms_per_t": ms / t_span, "ns_per_step_point": ms * 1e6 / (steps * npts), **errs(n, g)})
+        fd_dt = (TABLE2_FD_DT if fd_dts is None else fd_dts)[n]
+        steps = int(np.ceil(t_span / fd_dt))
+        prec = "f64" if steps <= fd_f64_max_steps else "f32"
+        if steps <= fd_max_steps:
+            row = {"grid": n, "scheme": "FD", "precision": prec, "dt": t_span / steps, "steps": steps}
+            try:
+                g, ms = _run(fs, problem(n, t_span / steps), f0 if prec == "f64" else f0.float(), steps, prec,
+                             scheme=fs.FS_SCHEME_EXPLICIT_FD)
+                row.update(ms=ms, ms_per_t=ms / t_span, ns_per_step_point=ms * 1e6 / (steps * npts), **errs(n, g))
+            except fs.FSError as e:  # a non-finite value: the FD step is unstable at this dt
+                row.update(unstable=str(e))
+            rows.append(row)
+        del f0
+    return {"workload": f"3D {l3d:g}^3, p = {p}, benchmark state at t = 1 (FD on {pre_n}^2 of the "
+                        f"{l2d:g}^2 domain) extruded by Eq. ic_eta_3d, t = 1 -> {1 + t_span:g}",
+            "reference": {"grid": nmax, "dt": ref_dt, "steps": ref_steps, "precision": "f64", "ms": ms_ref},
+            "rows": rows}
+
+
+def slab_study(steps: int = 20, grids=(1024, 2048), ranks=(1, 2, 4, 8)):
+    """Per-rank kernel time of the slab step: R ranks of one grid held by one
+    process, every rank's row pass (unpack, row kernel, pack) timed as one
+    group and every column pass as another, the L2 flushed before each step;
+    per rank = the group times / R (the GPU runs one rank's kernels at a
+    time, as each GPU would).  The exchanges between the groups are device
+    copies here (host-dispatch bound, not reported); between GPUs they are
+    (2 nf + 1) (R - 1) N s / R^2 bytes per rank and step (`exchange_bytes`)."""
+    import torch
+    from . import fs, inputs as I, slab as S
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    for n in grids:
+        pr = I.Problem(n=(n, n), p=2)
+        pr.dt = 6.0 * I.fd_stable_dt(pr)
+        f0 = torch.tensor(I.noise_fields(pr, seed=0), dtype=torch.float32, device="cuda")
+        plan = fs.Plan(pr, "f32")
+        plan.set_fields(f0)
+        plan.step(3)
+        plan_ms = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.step_async(1)
+            b.record()
+            torch.cuda.synchronize()
+            plan_ms += a.elapsed_time(b) / steps
+        plan.close()
+        for R in ranks:
+            L = S.LocalSlabs(pr, "f32", R)
+            L.set_fields(f0)
+            L.step(3)
+            row_ms = col_ms = 0.0
+            for _ in range(steps):
+                flush.fill_(1.0)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                ev[0].record()
+                for s in L.slabs:
+                    s.row_pass()
+                ev[1].record()
+                S.exchange_local_forward(L.lays, [s.send for s in L.slabs], [s.colspec for s in L.slabs])
+                ev[2].record()
+                for s in L.slabs:
+                    s.col_pass()
+                ev[3].record()
+                S.exchange_local_back(L.lays, [s.colspec for s in L.slabs], [s.recv for s in L.slabs])
+                torch.cuda.synchronize()
+                row_ms += ev[0].elapsed_time(ev[1]) / steps
+                col_ms += ev[2].elapsed_time(ev[3]) / steps
+            L.sync()
+            L.close()
+            fwd, back = L.lays[0].exchange_bytes(8)
+            rows.append({"grid": n, "ranks": R, "row_ms_per_rank": row_ms / R, "col_ms_per_rank": col_ms / R,
+                         "step_ms_per_rank": (row_ms + col_ms) / R, "plan_step_ms": plan_ms,
+                         "exchange_bytes_per_rank": fwd + back})
+    return {"workload": "2D n^2, p = 2, FP32, seeded +-0.01 noise, dt = 6 dt_FD; L2 flushed before each step",
+            "rows": rows}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2306_04322_gb300.experiments")
-    ap.add_argument("study", choices=["precision", "accuracy", "cost", "table1"])
+    ap.add_argument("study", choices=["precision", "accuracy", "cost", "table1", "table2", "slab"])
     ap.add_argument("--steps", type=int, default=None)
-    ap.add_argument("--t-span", type=float, default=1.0)
+    ap.add_argument("--t-span", type=float, default=None, help="time window (table1: 1, table2: 0.5)")
+    ap.add_argument("--fd-max-steps", type=int, default=100_000, help="table1: longest explicit FD run")
+    ap.add_argument("--fsfd-ref-dt-max-grid", type=int, default=None,
+                    help="table1: largest grid of the FS-FD forms at the reference dt")
     args = ap.parse_args(argv)
     from . import build as B
     B.build()
@@ -283,8 +441,13 @@ def main(argv=None):
         out = accuracy_study(args.steps or 10000)
     elif args.study == "cost":
         out = cost_study(args.steps or 200)
+    elif args.study == "slab":
+        out = slab_study(args.steps or 20)
+    elif args.study == "table2":
+        out = table2_study(args.t_span or 0.5)
     else:
-        out = table1_study(args.t_span)
+        out = table1_study(args.t_span or 1.0, fd_max_steps=args.fd_max_steps,
+                           fsfd_ref_dt_max_grid=args.fsfd_ref_dt_max_grid)
     print(json.dumps(out))
 
 

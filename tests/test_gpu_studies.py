@@ -60,3 +60,20 @@ def test_table1_study_small(X):
     assert fs64[1e-3]["E_eta"] < fs64[5e-3]["E_eta"]
     assert r["f32_floor"]["E_c"] < 1e-9 and r["f32_floor"]["E_eta"] < 1e-9
     assert {row["scheme"] for row in rows} == {"FS", "FSFD2", "FSFD4", "FD"}
+
+
+def test_table2_study_small(X):
+    """The Table 2 study on small cubes: every case yields finite errors and
+    timings, the FS time error grows with dt on the finest grid, and the
+    coarse grid's FS error is above the fine grid's."""
+    from paper_2306_04322_gb300 import inputs as I
+    fd = {n: 0.9 * I.fd_stable_dt(I.Problem(n=(n, n, n), dx=(100.0 / n,) * 3, p=4)) for n in (16, 32)}
+    r = X.table2_study(t_span=0.05, grids=(16, 32), fs_dt=5e-3, ref_dt=1e-3, pre_n=128, fd_dts=fd)
+    rows = r["rows"]
+    assert len(rows) == 2 * 3 + 2
+    for row in rows:
+        assert "unstable" not in row, row
+        assert math.isfinite(row["E_c"]) and math.isfinite(row["E_eta"]) and row["ms"] > 0
+    fs = {row["grid"]: row for row in rows if row["scheme"] == "FS"}
+    assert fs[16]["E_eta"] > fs[32]["E_eta"] > 0.0
+    assert {row["scheme"] for row in rows} == {"FS", "FSFD2", "FSFD4", "FD"}

@@ -50,3 +50,15 @@ def test_table1_constants_match_the_paper():
     assert tuple(sorted(fd2)) == X.TABLE1_GRIDS
     assert X.TABLE1_FD_DT == fd2
     assert X.TABLE1_FS_DTS == (1e-4, 1e-3, 5e-3)
+
+
+def test_table2_constants_match_the_paper():
+    """The 3D study's grids and FD time steps against the Table 2 fixture (the
+    3D rows of tests/golden/paper_fd_dt.txt, cube of edge 100)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_fd_dt.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    fd3 = {int(r[1]): float(r[3]) for r in rows if r[0] == "3"}
+    assert all(float(r[2]) == 100.0 for r in rows if r[0] == "3")
+    assert tuple(sorted(fd3)) == X.TABLE2_GRIDS
+    assert X.TABLE2_FD_DT == fd3
