@@ -247,10 +247,16 @@ FS_API fs_status fs_step2d_static(const fs_params* prm, void* fields, int64_t ns
  *       points);
  *   3 = form 2 with two warps per line (lines of 128 to 1024 points, and
  *       2D columns of 2048): half the values per thread, twice the warps;
+ *   4 = (both arguments) the fused step: the form-2 passes of every steady
+ *       step of an fs_step call in one cooperative launch, grid-wide
+ *       barriers between the passes (single 2D FS_F32 plans, square grids
+ *       of 256, 512 or 1024 points, p <= 3; the first step after
+ *       fs_set_fields runs the separate passes);
  *   0 = the default: form 2 for 2D lines of 256 to 1024 points, form 3 for
  *       2D columns of 2048, form 1 otherwise (3D x passes, with their many
  *       lines, keep form 1).
- * Form 2 on a plan it does not cover returns FS_ERR_UNSUPPORTED; FP64 plans
+ * A form on a plan it does not cover returns FS_ERR_UNSUPPORTED (form 4 for
+ * one pass only: FS_ERR_INVALID_ARG); FP64 plans
  * always run form 1.  On a batched plan a nonzero form pins the ensemble
  * kernels' form for that pass (the autotuner then only picks the grid size,
  * at the next fs_set_fields); 0 lets the autotuner choose.  Used by the
@@ -258,13 +264,15 @@ FS_API fs_status fs_step2d_static(const fs_params* prm, void* fields, int64_t ns
 FS_API fs_status fs_set_pass_forms(fs_plan_t plan, int row_form, int col_form);
 
 /* Test hook of the failure-detection path (the paper has no counterpart).
- * With enable != 0, the first bounded device wait of every pass this plan
+ * With enable = 1, the first bounded device wait of every pass this plan
  * launches gives up without polling: each pass sets the timeout flag, waits
  * (bounded) for its own copies to land and returns early, so the next
  * fs_step / fs_sync returns FS_ERR_TIMEOUT and the fields are unspecified.
- * enable = 0 restores the normal poll limit; set the fields again before
- * stepping on.  Nothing hangs or faults: no wait is removed, only the first
- * one is cut short.  Plans of one simulation only (batched plans return
+ * With enable = 2, only the grid-wide barriers of the fused step (pass form
+ * 4) give up without polling, with the same outcome.  enable = 0 restores
+ * the normal poll limits; set the fields again before stepping on.  Nothing
+ * hangs or faults: no wait is removed, only cut short.  Other values return
+ * FS_ERR_INVALID_ARG.  Plans of one simulation only (batched plans return
  * FS_ERR_UNSUPPORTED). */
 FS_API fs_status fs_test_short_wait(fs_plan_t plan, int enable);
 

@@ -63,9 +63,10 @@ struct KArgs {
   const double* csum;      // FP64 sum of c carried for the k = 0 mode (NULL: off)
   double* acc;             // FP64 accumulators of the free-energy diagnostic (2 + p)
   int* flag;               // sticky error bits (FS_FLAG_*)
-  int short_wait;          // test hook: nonzero makes the first bounded wait of every pass give up
+  int short_wait;          // test hook: 1 makes the first bounded wait of every pass give up
                            // without polling (the pass reports FS_FLAG_TIMEOUT; the kernels still
-                           // wait, bounded, for their own copies before exiting); 0 = normal
+                           // wait, bounded, for their own copies before exiting); 2 does the same
+                           // to the grid barriers of the fused step; 0 = normal
   long long spec_bytes;    // bytes of the buffer `spec` points into (index checks of FS_DEBUG_BOUNDS builds)
   long long real_bytes;    // bytes of the buffer `real` points into (same)
   Coef<float> cf;          // coefficients, FP32 copy
@@ -91,6 +92,14 @@ cudaError_t row2_launch_f32(const KArgs& a, cudaStream_t s);
 cudaError_t col2_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);
 bool row2_supported(int nx, int nf);
 bool col2_supported(int ny, int nf);
+// Fused step (pass form 4, fs_step2_f32.cu): `nsteps` steady-state steps
+// (mode 0) of a 2D FP32 plan in one cooperative launch, the pair-form row
+// pass and the warp-per-column pass separated by grid-wide barriers on the
+// two counters at gsync (zero between launches).  Square grids of 256, 512
+// or 1024 points, nf <= 4; needs tw_row2, tw_col2 and the two-column tensor
+// map.  cudaErrorNotSupported for other requests.
+bool step2_supported(int nx, int ny, int nf);
+cudaError_t step2_launch_f32(const KArgs& a, const CUtensorMap& tm, unsigned* gsync, int nsteps, cudaStream_t s);
 // Free-energy diagnostic, 2D (row pass mode 3 does the chemical sum and the
 // x transforms): y transforms and sums of w K2 |phi^|^2 per field.
 cudaError_t energy_col_launch_f32(const KArgs& a, const CUtensorMap& tm, cudaStream_t s);

@@ -93,7 +93,7 @@ struct Pointwise {
 // Polls of the first bounded wait of a pass: kWaitPolls, or none when the
 // plan's test hook asks every pass to report a timeout.  The wait that
 // follows a timeout (letting the CTA's own copies land) keeps kWaitPolls.
-__device__ __forceinline__ uint32_t first_wait_polls(const KArgs& a) { return a.short_wait ? 0u : kWaitPolls; }
+__device__ __forceinline__ uint32_t first_wait_polls(const KArgs& a) { return (a.short_wait & 1) ? 0u : kWaitPolls; }
 
 // Index checks of the bounds-checked build (compiled with FS_DEBUG_BOUNDS):
 // an access of `bytes` at p outside [base, base + extent) sets

@@ -82,6 +82,7 @@ struct fs_plan {
   std::vector<void*> blocks;
   size_t ws_bytes = 0;
   int* flag = nullptr;
+  unsigned* gsync = nullptr; // grid-barrier counters of the fused step (pass form 4)
   double* acc = nullptr;     // diagnostic accumulators (device)
   int* host_flag = nullptr;  // pinned
   int state = kStateNone;
@@ -90,7 +91,7 @@ struct fs_plan {
   int64_t last_launches = 0;
   int short_wait = 0;  // test hook of fs_test_short_wait
   int row_form = 0;    // fs_set_pass_forms: 0 default, 1 half-length / tile kernels, 2 warp-per-line
-                       // kernels, 3 the same with two warps per line
+                       // kernels, 3 the same with two warps per line, 4 (both passes) the fused step
   int col_form = 0;
   std::vector<cudaEvent_t> ev_pool;  // fs_step_profiled timing events
   std::vector<int> ev_kind;
@@ -264,8 +265,9 @@ fs::KArgs make_args(const fs_plan* p, const Member& m, int mode) {
   // several-row CTAs of the half-length kernel there -- always with form 2,
   // never with form 1; ensemble members keep both tables (the autotuner
   // picks the form per pass)
-  const bool r2 = p->batch || p->row_form == 2 || (p->row_form == 0 && m.prm.n[0] >= 256 && m.prm.ndim == 2);
-  const bool c2 = p->batch || p->col_form == 2 || (p->col_form == 0 && m.prm.n[1] >= 256);
+  const bool r2 = p->batch || p->row_form == 2 || p->row_form == 4 ||
+                  (p->row_form == 0 && m.prm.n[0] >= 256 && m.prm.ndim == 2);
+  const bool c2 = p->batch || p->col_form == 2 || p->col_form == 4 || (p->col_form == 0 && m.prm.n[1] >= 256);
   a.tw_row2 = r2 ? m.tw_row2 : nullptr;
   a.tw_col2 = c2 ? m.tw_col2 : nullptr;
   a.tw_row2w = (!p->batch && p->row_form == 3) ? m.tw_row2w : nullptr;
@@ -467,6 +469,21 @@ cudaError_t enqueue_step(fs_plan* p, int mode, cudaStream_t s, int64_t* launches
   return cudaSuccess;
 }
 
+// Pass form 4: `nsteps` steady-state steps of a single 2D FP32 plan in one
+// cooperative launch (row pass, grid barrier, column pass per step).
+bool fused(const fs_plan* p) { return p->row_form == 4; }
+cudaError_t launch_fused(const fs_plan* p, int64_t nsteps, cudaStream_t s) {
+  const Member& m = p->members[0];
+  const fs::KArgs a = make_args(p, m, 0);
+  for (int64_t left = nsteps; left > 0;) {
+    const int n = left > (1 << 30) ? (1 << 30) : (int)left;
+    cudaError_t e = fs::step2_launch_f32(a, m.tmap_col2, p->gsync, n, s);
+    if (e != cudaSuccess) return e;
+    left -= n;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_pass(const fs_plan* p, const Member& m, const fs::KArgs& a, int kind, cudaStream_t s) {
   if (kind == 0) return launch_row(p, a, s);
   if (m.prm.ndim == 2) return launch_col(p, m, a, s);
@@ -524,7 +541,10 @@ fs_status read_flag(fs_plan* p) {
   int f = *p->host_flag;
   if (f) {
     cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream);
-    if (f & fs::FS_FLAG_TIMEOUT) return fail(p, FS_ERR_TIMEOUT, "a bounded device wait timed out");
+    if (f & fs::FS_FLAG_TIMEOUT) {
+      cudaMemsetAsync(p->gsync, 0, 2 * sizeof(unsigned), p->stream);  // a fused step may have left a barrier open
+      return fail(p, FS_ERR_TIMEOUT, "a bounded device wait timed out");
+    }
     if (f & fs::FS_FLAG_NONFINITE) return fail(p, FS_ERR_NONFINITE, "non-finite value in the fields");
     return fail(p, FS_ERR_CUDA, "device reported an index out of bounds");
   }
@@ -1008,7 +1028,8 @@ fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc
   }
   p->flag = (int*)plan_alloc(p, 256);
   p->acc = (double*)plan_alloc(p, 256);
-  if (!p->flag || !p->acc) {
+  p->gsync = (unsigned*)plan_alloc(p, 256);
+  if (!p->flag || !p->acc || !p->gsync) {
     plan_free_all(p);
     delete p;
     return fail(nullptr, FS_ERR_OOM, "device workspace allocation failed");
@@ -1025,6 +1046,7 @@ fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc
     if (e == cudaSuccess && !encode_col_map(p->members[i], p->nf + 1, p->f64)) e = cudaErrorInvalidValue;
   }
   if (e == cudaSuccess) e = cudaMemset(p->flag, 0, 256);
+  if (e == cudaSuccess) e = cudaMemset(p->gsync, 0, 256);
   if (e != cudaSuccess) {
     fs_status s = cuda_fail(nullptr, e, "plan tables");
     cudaFreeHost(p->host_flag);
@@ -1119,6 +1141,12 @@ fs_status fs_step_async(fs_plan_t p, int64_t nsteps) {
     p->state = kStateSpec;
   }
   int64_t left = nsteps - done;
+  if (left > 0 && fused(p)) {
+    e = launch_fused(p, left, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "fused step launch");
+    launches += 1;
+    left = 0;
+  }
   if (left >= kGraphSteps && !p->fd) {
     if (!p->gexec) {
       e = build_graph(p);
@@ -1361,6 +1389,13 @@ fs_status fs_step_profiled(fs_plan_t p, int64_t nsteps) {
   }
   for (int64_t s = 0; s < nsteps && e == cudaSuccess && !p->batch; ++s) {
     int mode = p->state == kStateReal ? 1 : 0;
+    if (mode == 0 && fused(p)) {  // one launch per step, timed as pass 0
+      rec(0);
+      if (e == cudaSuccess) e = launch_fused(p, 1, p->stream);
+      rec(0);
+      launches++;
+      continue;
+    }
     for (const Member& m : p->members) {
       fs::KArgs a = make_args(p, m, mode);
       for (int k = 0; k < pass_kinds(m); ++k) {
@@ -1405,10 +1440,14 @@ fs_status fs_profile_read(fs_plan_t p, double* ms_per_pass, int64_t* launches_pe
 
 fs_status fs_set_pass_forms(fs_plan_t p, int row_form, int col_form) {
   if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
-  if (row_form < 0 || row_form > 3 || col_form < 0 || col_form > 3)
+  if (row_form < 0 || row_form > 4 || col_form < 0 || col_form > 4 || ((row_form == 4) != (col_form == 4)))
     return fail(p, FS_ERR_INVALID_ARG,
-                "pass forms are 0 (default), 1 (half-length / tile), 2 (warp per line), 3 (two warps per line)");
+                "pass forms are 0 (default), 1 (half-length / tile), 2 (warp per line), 3 (two warps per line), "
+                "4 for both passes (fused step)");
   const Member& m = p->members[0];
+  if (row_form == 4 && (p->batch || p->f64 || m.prm.ndim != 2 || !m.tw_row2 || !m.tw_col2 ||
+                        !fs::step2_supported(m.prm.n[0], m.prm.n[1], p->nf)))
+    return fail(p, FS_ERR_UNSUPPORTED, "the fused step covers single 2D FP32 plans of 256^2, 512^2 or 1024^2, p <= 3");
   const bool r2ok = p->batch ? p->bargs.maps2 != nullptr : m.tw_row2 != nullptr;
   const bool c2ok = p->batch ? p->bargs.maps2 != nullptr : m.tw_col2 != nullptr;
   const bool r3ok = !p->batch && m.tw_row2w != nullptr, c3ok = !p->batch && m.tw_col2w != nullptr;
@@ -1424,7 +1463,8 @@ fs_status fs_set_pass_forms(fs_plan_t p, int row_form, int col_form) {
 fs_status fs_test_short_wait(fs_plan_t p, int enable) {
   if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
   if (p->batch) return fail(p, FS_ERR_UNSUPPORTED, "fs_test_short_wait is built for plans of one simulation");
-  p->short_wait = enable ? 1 : 0;
+  if (enable < 0 || enable > 2) return fail(p, FS_ERR_INVALID_ARG, "enable must be 0, 1 or 2");
+  p->short_wait = enable;
   drop_graph(p);  // the captured launches hold the arguments by value
   return FS_OK;
 }

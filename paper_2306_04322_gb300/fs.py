@@ -265,9 +265,10 @@ def fs_set_pass_forms(plan, row_form: int, col_form: int):
     _check(lib().fs_set_pass_forms(plan, int(row_form), int(col_form)), plan)
 
 
-def fs_test_short_wait(plan, enable: bool):
-    """Test hook: cut the first bounded device wait of every pass short."""
-    _check(lib().fs_test_short_wait(plan, 1 if enable else 0), plan)
+def fs_test_short_wait(plan, enable):
+    """Test hook: 1 (or True) cuts the first bounded device wait of every pass
+    short, 2 the grid barriers of the fused step, 0 (False) restores both."""
+    _check(lib().fs_test_short_wait(plan, int(enable)), plan)
 
 
 def fs_measure_fp64_rate(stream=None):

@@ -1,9 +1,11 @@
-"""Both kernel forms of the FP32 passes against the FP64 oracle.
+"""The kernel forms of the FP32 passes against the FP64 oracle.
 
 Form 1: the half-length row pass (one real row as a complex line of nx/2) and
 the column-tile pass.  Form 2: the pair-form row pass (two rows as one complex
 line of nx) and the warp-per-column pass; form 3 the same with two warps per
-line.  Both compute Algorithm 1; only the
+line; form 4 the form-2 passes fused into one cooperative launch per call
+(grid-wide barriers between the passes and steps).  All compute Algorithm 1;
+only the
 rounding order differs.  Each grid is run through the first step from the
 real fields (row mode 1), steady steps (mode 0) and the final inverse row pass
 (mode 2, fs_get_fields), for p = 0..4.
@@ -134,3 +136,75 @@ def test_forms_graph_path_headline(F, O):
         e = rel_linf(g, ref)
         print(f"1024^2 forms {forms}: 34 steps {e:.2e}")
         assert e <= bound(34)
+
+
+@pytest.mark.parametrize("n,p", [((256, 256), 2), ((512, 512), 3), ((1024, 1024), 2), ((256, 256), 0)])
+def test_fused_step_matches_the_oracle(F, O, n, p):
+    """Form 4: the first step from the real fields runs the separate passes,
+    the next ones one fused launch per call (1 step, then 5 in one launch)."""
+    pr = I.Problem(n=n, p=p)
+    pr.dt = 5.0 * I.fd_stable_dt(pr)
+    f0 = I.noise_fields(pr, seed=23)
+    r2, _ = O.step(pr, f0, 2)
+    r7, _ = O.step(pr, r2, 5)
+    g2, g7 = run(F, pr, f0.astype(np.float32), (4, 4), [2, 5])
+    assert rel_linf(g2, r2) <= bound(2)
+    assert rel_linf(g7, r7) <= bound(7)
+
+
+def test_fused_step_headline_long_launch(F, O):
+    """The benchmark's workload, 34 steps of which 33 in one launch, against
+    the oracle and against the separate form-2 passes."""
+    pr = I.Problem(n=(1024, 1024), p=2)
+    pr.dt = 6.0 * I.fd_stable_dt(pr)
+    f0 = I.noise_fields(pr, seed=0)
+    ref, _ = O.step(pr, f0, 34)
+    (g4,) = run(F, pr, f0.astype(np.float32), (4, 4), [34])
+    (g2,) = run(F, pr, f0.astype(np.float32), (2, 2), [34])
+    assert rel_linf(g4, ref) <= bound(34)
+    # the same bodies in the same order: identical up to the compiler's
+    # instruction choices in the two kernels
+    print("fused vs separate passes: identical" if np.array_equal(g4, g2) else
+          f"fused vs separate passes: {rel_linf(g4, g2):.2e}")
+    assert rel_linf(g4, g2) <= bound(34)
+
+
+def test_fused_step_selector_and_timeout(F):
+    import torch
+    for n, p, prec in [((512, 256), 2, "f32"), ((256, 256), 4, "f32"), ((256, 256), 2, "f64"),
+                       ((128, 128), 1, "f32"), ((256, 256), 1, "tf32")]:
+        plan = F.Plan(I.Problem(n=n, p=p, dt=1e-3), prec)
+        with pytest.raises(F.FSError) as ei:
+            F.fs_set_pass_forms(plan.h, 4, 4)
+        assert ei.value.status == F.FS_ERR_UNSUPPORTED, (n, p, prec)
+        plan.close()
+    plan = F.Plan(I.Problem(n=(256, 256), p=1, dt=1e-3), "f32")
+    with pytest.raises(F.FSError) as ei:
+        F.fs_set_pass_forms(plan.h, 4, 2)
+    assert ei.value.status == F.FS_ERR_INVALID_ARG
+    # the timeout hook cuts the fused launch short too; the plan recovers
+    pr = I.Problem(n=(256, 256), p=1)
+    pr.dt = 5.0 * I.fd_stable_dt(pr)
+    f0 = torch.tensor(I.noise_fields(pr, seed=24), dtype=torch.float32, device="cuda")
+    F.fs_set_pass_forms(plan.h, 4, 4)
+    plan.set_fields(f0)
+    plan.step(2)
+    F.fs_test_short_wait(plan.h, True)
+    with pytest.raises(F.FSError) as ei:
+        plan.step(5)
+    assert ei.value.status == F.FS_ERR_TIMEOUT
+    F.fs_test_short_wait(plan.h, False)
+    plan.set_fields(f0)
+    plan.step(6)
+    # the grid barriers alone give up: the launch ends, the status says so
+    F.fs_test_short_wait(plan.h, 2)
+    with pytest.raises(F.FSError) as ei:
+        plan.step(5)
+    assert ei.value.status == F.FS_ERR_TIMEOUT
+    F.fs_test_short_wait(plan.h, 0)
+    plan.set_fields(f0)
+    plan.step(6)
+    with pytest.raises(F.FSError) as ei:
+        F.fs_test_short_wait(plan.h, 3)
+    assert ei.value.status == F.FS_ERR_INVALID_ARG
+    plan.close()
