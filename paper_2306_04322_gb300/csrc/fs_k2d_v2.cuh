@@ -254,8 +254,16 @@ __device__ __forceinline__ bool row2_body(const KArgs& a, long long pair, unsign
   return true;
 }
 
-template <int NX, int G>
-__global__ void __launch_bounds__(Row2Cfg<NX, G>::MAX_THREADS, G == 1 ? 3 : 2) fs_row2_kernel(KArgs a) {
+// NW: the most warps per line group the instantiation takes (nf <= NW).
+// With one warp per line and nf = 3 the register budget is that of four
+// 96-thread CTAs per SM (170 per thread; a pass of 1024 rows stays one
+// wave), which leaves the compiler room to schedule the values of each
+// thread; otherwise three 160-thread CTAs (136).  Measured (L2 flushed
+// before each step, p = 2): 512^2 step 17.1 us against 19.1 us, 1024^2
+// unchanged; with nf = 2 the 1024^2 step lost 4 %, so only nf = 3 takes it.
+template <int NX, int G, int NW>
+__global__ void __launch_bounds__(32 * G * NW, (G == 1 && NW <= 3) ? 4 : (G == 1 ? 3 : 2))
+    fs_row2_kernel(KArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   if (threadIdx.x == 0) {
@@ -476,13 +484,18 @@ __global__ void __launch_bounds__(128 * G, Col2Cfg<NY, G>::MIN_BLOCKS)
 
 // Launchers: cudaErrorNotSupported when this form does not cover the
 // request (the caller falls back to the half-length / tile kernels).
+template <int NX, int G, int NW>
+cudaError_t row2_launch_nw(const KArgs& a, cudaStream_t s) {
+  static unsigned done = 0;
+  cudaError_t e = allow_big_smem(fs_row2_kernel<NX, G, NW>, &done);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(fs_row2_kernel<NX, G, NW>, dim3((unsigned)(a.lines / 2)), dim3((unsigned)(32 * G * a.nf)),
+                    row2_smem_bytes<NX, G>(a.nf), s, a);
+}
 template <int NX, int G>
 cudaError_t row2_launch_n(const KArgs& a, cudaStream_t s) {
-  static unsigned done = 0;
-  cudaError_t e = allow_big_smem(fs_row2_kernel<NX, G>, &done);
-  if (e != cudaSuccess) return e;
-  return launch_pdl(fs_row2_kernel<NX, G>, dim3((unsigned)(a.lines / 2)), dim3((unsigned)(32 * G * a.nf)),
-                    row2_smem_bytes<NX, G>(a.nf), s, a);
+  if (G == 1 && a.nf == 3) return row2_launch_nw<NX, G, 3>(a, s);
+  return row2_launch_nw<NX, G, 5>(a, s);
 }
 
 template <int NY, int G>
