@@ -76,8 +76,12 @@ struct LineSync {
 // layout), then the pair values in natural order for the pointwise stage.
 // `bar` is an initialised mbarrier whose next phase has parity `parity`; the
 // ensemble kernel calls this once per work item.  Returns false if a bounded
-// wait gave up.
-template <int NX, int G = 1>
+// wait gave up.  PC >= 0: p is known to be PC at compile time (the
+// pointwise stage then takes kRow2PointsPerIter grid-point pairs per iteration, unrolled
+// over the fields); -1: p = nf - 1 at run time.
+constexpr int kRow2PointsPerIter = 4;
+
+template <int NX, int G = 1, int PC = -1>
 __device__ __forceinline__ bool row2_body(const KArgs& a, long long pair, unsigned char* smem_raw, uint64_t* bar,
                                           uint32_t parity) {
   using C = float2;
@@ -229,6 +233,46 @@ __device__ __forceinline__ bool row2_body(const KArgs& a, long long pair, unsign
 
     // pointwise stage: pairs (row a, row b) of every field, lane-wise
     const Pointwise<float> pw(a);
+    if constexpr (PC >= 0) {
+      // U independent points per iteration: all loads, then the arithmetic
+      // of all, then the stores (points past the row repeat point n)
+      constexpr int P = PC, PE = PC > 0 ? PC : 1, U = kRow2PointsPerIter;
+      for (int n = threadIdx.x; n < NX; n += U * blockDim.x) {
+        int k[U];
+        C c[U], e[U][PE], h[U], S2[U], fc[U], g[U][PE];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          k[u] = n + u * (int)blockDim.x < NX ? n + u * (int)blockDim.x : n;
+          c[u] = areas[k[u]];
+#pragma unroll
+          for (int i = 0; i < P; ++i) e[u][i] = areas[(1 + i) * PL + k[u]];
+        }
+        float chk = 0.f;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          h[u] = vsplat<C>(0.f);
+          S2[u] = vsplat<C>(0.f);
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            h[u] = cadd(h[u], pw.hpoly2(e[u][i]));
+            S2[u] = vfma(e[u][i], e[u][i], S2[u]);
+          }
+          fc[u] = pw.fc2(c[u], h[u]);
+          chk += fc[u].x + fc[u].y;
+#pragma unroll
+          for (int i = 0; i < P; ++i) g[u][i] = pw.g2(c[u], e[u][i], S2[u]);
+        }
+        bad |= !finite_val(chk);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          areas[nf * PL + k[u]] = fc[u];
+#pragma unroll
+          for (int i = 0; i < P; ++i) areas[(1 + i) * PL + k[u]] = g[u][i];
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     const int p = nf - 1;
     for (int n = threadIdx.x; n < NX; n += blockDim.x) {
       const C c = areas[n];
@@ -271,7 +315,7 @@ __global__ void __launch_bounds__(32 * G * NW, (G == 1 && NW <= 3) ? 4 : (G == 1
     fence_mbar_init();
   }
   __syncthreads();
-  row2_body<NX, G>(a, blockIdx.x, smem_raw, bar, 0);
+  row2_body<NX, G, (G == 1 && NW == 3) ? 2 : -1>(a, blockIdx.x, smem_raw, bar, 0);
 }
 
 template <int NY, int G = 1>
