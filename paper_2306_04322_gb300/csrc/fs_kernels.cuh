@@ -211,6 +211,49 @@ __device__ __forceinline__ void row_issue(const KArgs& a, long long rb, cplx<T>*
   }
 }
 
+// Pointwise stage of the half-length row pass with p = P known at compile
+// time: U independent points per iteration -- all loads, then the
+// arithmetic, then the stores (points past the end repeat idx).  in: the
+// field slots [nf][R][PL] (eta_i replaced by g_i), scr: df/dc [R][PL].
+template <typename T, int P, int U, int R, int PL, int L>
+__device__ __forceinline__ void row_pointwise_fixed(const Pointwise<T>& pw, cplx<T>* in, cplx<T>* scr, int n,
+                                                    bool& bad) {
+  using C = cplx<T>;
+  for (int idx = threadIdx.x; idx < n; idx += U * blockDim.x) {
+    int off[U];
+    C c[U], e[U][P], fc[U], gv[U][P];
+    T chk = T(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = idx + u * (int)blockDim.x < n ? idx + u * (int)blockDim.x : idx;
+      off[u] = (j / L) * PL + j % L;
+      c[u] = in[off[u]];
+#pragma unroll
+      for (int i = 0; i < P; ++i) e[u][i] = in[(1 + i) * R * PL + off[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      C h = vsplat<C>(T(0)), S2 = vsplat<C>(T(0));
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        h = cadd(h, pw.hpoly2(e[u][i]));
+        S2 = vfma(e[u][i], e[u][i], S2);
+      }
+      fc[u] = pw.fc2(c[u], h);
+      chk += fc[u].x + fc[u].y;  // non-finite whenever any input is (see the runtime loop)
+#pragma unroll
+      for (int i = 0; i < P; ++i) gv[u][i] = pw.g2(c[u], e[u][i], S2);
+    }
+    bad |= !finite_val(chk);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      scr[off[u]] = fc[u];
+#pragma unroll
+      for (int i = 0; i < P; ++i) in[(1 + i) * R * PL + off[u]] = gv[u][i];
+    }
+  }
+}
+
 // Compute part of one row-pass work item (row block rb) once its rows have
 // landed: input slots `in` ([nf][R][PL], fields in natural layout), scratch
 // slot `scr` ([R][PL], df/dc), pass tables `twr` in shared memory.
@@ -367,45 +410,10 @@ __device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T
       for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
       if (lane == 0) atomicAdd(&a.acc[0], sum);
     } else if (nf == 3) {
-      // p = 2 (the configurations' field count) with p known at compile
-      // time: U independent points per iteration, all loads, then the
-      // arithmetic, then the stores (points past the end repeat idx)
-      constexpr int P = 2, U = 4;
-      const Pointwise<T> pw(a);
-      const int n = Reff * L;
-      for (int idx = threadIdx.x; idx < n; idx += U * blockDim.x) {
-        int off[U];
-        C c[U], e[U][P], fc[U], gv[U][P];
-        T chk = T(0);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int j = idx + u * (int)blockDim.x < n ? idx + u * (int)blockDim.x : idx;
-          off[u] = (j / L) * PL + j % L;
-          c[u] = in[off[u]];
-#pragma unroll
-          for (int i = 0; i < P; ++i) e[u][i] = in[(1 + i) * R * PL + off[u]];
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          C h = vsplat<C>(T(0)), S2 = vsplat<C>(T(0));
-#pragma unroll
-          for (int i = 0; i < P; ++i) {
-            h = cadd(h, pw.hpoly2(e[u][i]));
-            S2 = vfma(e[u][i], e[u][i], S2);
-          }
-          fc[u] = pw.fc2(c[u], h);
-          chk += fc[u].x + fc[u].y;
-#pragma unroll
-          for (int i = 0; i < P; ++i) gv[u][i] = pw.g2(c[u], e[u][i], S2);
-        }
-        bad |= !finite_val(chk);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          scr[off[u]] = fc[u];
-#pragma unroll
-          for (int i = 0; i < P; ++i) in[(1 + i) * R * PL + off[u]] = gv[u][i];
-        }
-      }
+      // the configurations' field counts with p known at compile time
+      row_pointwise_fixed<T, 2, 4, R, PL, L>(Pointwise<T>(a), in, scr, Reff * L, bad);
+    } else if (nf == 5) {
+      row_pointwise_fixed<T, 4, 2, R, PL, L>(Pointwise<T>(a), in, scr, Reff * L, bad);
     } else {
       const Pointwise<T> pw(a);
       const int p = nf - 1;
