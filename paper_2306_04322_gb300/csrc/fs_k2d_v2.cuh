@@ -70,17 +70,60 @@ struct LineSync {
   }
 };
 
+// Pointwise stage of the pair-form row pass (Section 2.1 derivatives, lane-
+// wise on the two rows of a pair) with p = P known at compile time: four
+// independent points per iteration -- all loads, then the arithmetic, then
+// the stores (points past the row repeat point n).  areas: [nf + 1][PL],
+// c, eta_i (replaced by g_i), df/dc in area nf.  df/dc is non-finite
+// whenever c or any eta_i is (see the row pass of fs_kernels.cuh): one test
+// of the sum of its lanes covers all inputs.
+template <int P, int NX, int PL>
+__device__ __forceinline__ void row2_pointwise_fixed(const Pointwise<float>& pw, float2* areas, bool& bad) {
+  using C = float2;
+  constexpr int PE = P > 0 ? P : 1, U = 4;
+  for (int n = threadIdx.x; n < NX; n += U * blockDim.x) {
+    int k[U];
+    C c[U], e[U][PE], fc[U], g[U][PE];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      k[u] = n + u * (int)blockDim.x < NX ? n + u * (int)blockDim.x : n;
+      c[u] = areas[k[u]];
+#pragma unroll
+      for (int i = 0; i < P; ++i) e[u][i] = areas[(1 + i) * PL + k[u]];
+    }
+    float chk = 0.f;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      C h = vsplat<C>(0.f), S2 = vsplat<C>(0.f);
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        h = cadd(h, pw.hpoly2(e[u][i]));
+        S2 = vfma(e[u][i], e[u][i], S2);
+      }
+      fc[u] = pw.fc2(c[u], h);
+      chk += fc[u].x + fc[u].y;
+#pragma unroll
+      for (int i = 0; i < P; ++i) g[u][i] = pw.g2(c[u], e[u][i], S2);
+    }
+    bad |= !finite_val(chk);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      areas[(P + 1) * PL + k[u]] = fc[u];
+#pragma unroll
+      for (int i = 0; i < P; ++i) areas[(1 + i) * PL + k[u]] = g[u][i];
+    }
+  }
+}
+
 // One row pair (rows 2 pair and 2 pair + 1) of the simulation `a`, one warp
 // per field (blockDim = 32 nf).  Field areas [nf + 1][PL] (the last one holds
 // df/dc): staging of the bulk copies, then the warp's exchange buffer (pad32
 // layout), then the pair values in natural order for the pointwise stage.
 // `bar` is an initialised mbarrier whose next phase has parity `parity`; the
 // ensemble kernel calls this once per work item.  Returns false if a bounded
-// wait gave up.  PC >= 0: p is known to be PC at compile time (the
-// pointwise stage then takes kRow2PointsPerIter grid-point pairs per iteration, unrolled
-// over the fields); -1: p = nf - 1 at run time.
-constexpr int kRow2PointsPerIter = 4;
-
+// wait gave up.  PC >= 0: the caller guarantees nf = PC + 1, and the
+// pointwise stage is compiled for that p alone (the 96-thread kernel, whose
+// nf is 3: a kernel holding the code for every p measured slower there).
 template <int NX, int G = 1, int PC = -1>
 __device__ __forceinline__ bool row2_body(const KArgs& a, long long pair, unsigned char* smem_raw, uint64_t* bar,
                                           uint32_t parity) {
@@ -234,62 +277,15 @@ __device__ __forceinline__ bool row2_body(const KArgs& a, long long pair, unsign
     // pointwise stage: pairs (row a, row b) of every field, lane-wise
     const Pointwise<float> pw(a);
     if constexpr (PC >= 0) {
-      // U independent points per iteration: all loads, then the arithmetic
-      // of all, then the stores (points past the row repeat point n)
-      constexpr int P = PC, PE = PC > 0 ? PC : 1, U = kRow2PointsPerIter;
-      for (int n = threadIdx.x; n < NX; n += U * blockDim.x) {
-        int k[U];
-        C c[U], e[U][PE], h[U], S2[U], fc[U], g[U][PE];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          k[u] = n + u * (int)blockDim.x < NX ? n + u * (int)blockDim.x : n;
-          c[u] = areas[k[u]];
-#pragma unroll
-          for (int i = 0; i < P; ++i) e[u][i] = areas[(1 + i) * PL + k[u]];
-        }
-        float chk = 0.f;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          h[u] = vsplat<C>(0.f);
-          S2[u] = vsplat<C>(0.f);
-#pragma unroll
-          for (int i = 0; i < P; ++i) {
-            h[u] = cadd(h[u], pw.hpoly2(e[u][i]));
-            S2[u] = vfma(e[u][i], e[u][i], S2[u]);
-          }
-          fc[u] = pw.fc2(c[u], h[u]);
-          chk += fc[u].x + fc[u].y;
-#pragma unroll
-          for (int i = 0; i < P; ++i) g[u][i] = pw.g2(c[u], e[u][i], S2[u]);
-        }
-        bad |= !finite_val(chk);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          areas[nf * PL + k[u]] = fc[u];
-#pragma unroll
-          for (int i = 0; i < P; ++i) areas[(1 + i) * PL + k[u]] = g[u][i];
-        }
-      }
-      __syncthreads();
-      continue;
-    }
-    const int p = nf - 1;
-    for (int n = threadIdx.x; n < NX; n += blockDim.x) {
-      const C c = areas[n];
-      C h = vsplat<C>(0.f), S2 = vsplat<C>(0.f);
-      for (int i = 0; i < p; ++i) {
-        const C e = areas[(1 + i) * PL + n];
-        h = cadd(h, pw.hpoly2(e));
-        S2 = vfma(e, e, S2);
-      }
-      // df/dc is non-finite whenever c or any eta_i is (see the row pass of
-      // fs_kernels.cuh): one test of its two lanes' sum covers all inputs
-      const C fc = pw.fc2(c, h);
-      bad |= !finite_val(fc.x + fc.y);
-      areas[nf * PL + n] = fc;
-      for (int i = 0; i < p; ++i) {
-        const C e = areas[(1 + i) * PL + n];
-        areas[(1 + i) * PL + n] = pw.g2(c, e, S2);
+      row2_pointwise_fixed<PC, NX, PL>(pw, areas, bad);
+    } else {
+      switch (nf) {  // p known at compile time for every supported field count
+        case 1: row2_pointwise_fixed<0, NX, PL>(pw, areas, bad); break;
+        case 2: row2_pointwise_fixed<1, NX, PL>(pw, areas, bad); break;
+        case 3: row2_pointwise_fixed<2, NX, PL>(pw, areas, bad); break;
+        case 4: row2_pointwise_fixed<3, NX, PL>(pw, areas, bad); break;
+        case 5: row2_pointwise_fixed<4, NX, PL>(pw, areas, bad); break;
+        default: break;
       }
     }
     __syncthreads();

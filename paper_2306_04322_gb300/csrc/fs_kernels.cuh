@@ -409,11 +409,16 @@ __device__ __forceinline__ void row_compute(const KArgs& a, long long rb, cplx<T
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
       if (lane == 0) atomicAdd(&a.acc[0], sum);
-    } else if (nf == 3) {
-      // the configurations' field counts with p known at compile time
-      row_pointwise_fixed<T, 2, 4, R, PL, L>(Pointwise<T>(a), in, scr, Reff * L, bad);
-    } else if (nf == 5) {
-      row_pointwise_fixed<T, 4, 2, R, PL, L>(Pointwise<T>(a), in, scr, Reff * L, bad);
+    } else if (sizeof(T) == 4 && nf >= 2) {
+      // FP32: p known at compile time for every supported field count (FP64
+      // is bound by its arithmetic pipe and keeps the loop below)
+      const Pointwise<T> pw(a);
+      switch (nf) {
+        case 2: row_pointwise_fixed<T, 1, 4, R, PL, L>(pw, in, scr, Reff * L, bad); break;
+        case 3: row_pointwise_fixed<T, 2, 4, R, PL, L>(pw, in, scr, Reff * L, bad); break;
+        case 4: row_pointwise_fixed<T, 3, 2, R, PL, L>(pw, in, scr, Reff * L, bad); break;
+        default: row_pointwise_fixed<T, 4, 2, R, PL, L>(pw, in, scr, Reff * L, bad); break;
+      }
     } else {
       const Pointwise<T> pw(a);
       const int p = nf - 1;
