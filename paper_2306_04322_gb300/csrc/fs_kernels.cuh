@@ -543,14 +543,20 @@ struct KUpdate {
   // zc = c^ / (2 nx) in the units of zf
   template <typename C>
   __device__ __forceinline__ C c(C zc, C zf, T k2) const {
-    T d = scale_c / (T(1) + Mdtkc * k2 * k2);
+    T d = quot(scale_c, T(1) + Mdtkc * k2 * k2);
     T b = Mdt_c * k2;
     return cscale(vfma(zf, vsplat<C>(-b), zc), d);
   }
   // eta^' = g^ / (1 + L dt kappa_eta K2), times the 1/(2N) scale
   template <typename C>
   __device__ __forceinline__ C eta(C zg, T k2) const {
-    return cscale(zg, scale / (T(1) + Ldtke * k2));
+    return cscale(zg, quot(scale, T(1) + Ldtke * k2));
+  }
+  // x / y for the denominators above (y >= 1): FP32 through the fast
+  // reciprocal (2 ulp, as the warp-per-column pass), FP64 rounded
+  __device__ __forceinline__ static T quot(T x, T y) {
+    if constexpr (sizeof(T) == 4) return __fdividef(x, y);
+    else return x / y;
   }
 };
 
