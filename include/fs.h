@@ -179,9 +179,10 @@ FS_API fs_status fs_free_energy(fs_plan_t plan, double* F, double* parts);
  * += d<lambda_in, step(u)>/d(M, L, kappa_c, kappa_eta).  The paper has no
  * adjoint; this is the transpose of the Jacobian of the Algorithm-1 step.
  * Uses the plan's workspace (the plan's own state is not modified).
- * Synchronises when grad_theta is not NULL.  Built for 2D semi-implicit FS
- * plans of one simulation with axes up to 1024; others return
- * FS_ERR_UNSUPPORTED. */
+ * Synchronises when grad_theta is not NULL.  Built for 2D and 3D
+ * semi-implicit FS plans of one simulation (2D axes up to 1024; the 3D limits
+ * of the plans, with |xi|^2 of Eq. (Gamma_fft_3d) or its FS-FD forms); others
+ * return FS_ERR_UNSUPPORTED. */
 FS_API fs_status fs_step_adjoint(fs_plan_t plan, const void* const* u, const void* const* lambda_in,
                           void* const* lambda_out, double grad_theta[4]);
 

@@ -5,4 +5,8 @@ namespace fs {
 cudaError_t adjoint_launch_f64(const KArgs& a, const CUtensorMap& tm, void* lam_out, cudaStream_t s) {
   return adjoint_launch_t<double>(a, tm, lam_out, s);
 }
+cudaError_t adjoint3_launch_f64(const KArgs& a, const CUtensorMap& tm_y, const CUtensorMap& tm_z, void* lam_out,
+                               cudaStream_t s) {
+  return adjoint3_launch_t<double>(a, tm_y, tm_z, lam_out, s);
+}
 }  // namespace fs

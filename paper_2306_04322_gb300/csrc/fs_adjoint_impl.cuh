@@ -2,6 +2,7 @@
 #pragma once
 
 #include "fs_adjoint.cuh"
+#include "fs_adjoint3.cuh"
 #include "fs_k2d_impl.cuh"
 
 namespace fs {
@@ -66,6 +67,67 @@ cudaError_t adjoint_launch_t(const KArgs& a0, const CUtensorMap& tm, void* lam_o
 #undef FS_CASE
     default: break;
   }
+  if (e != cudaSuccess) return e;
+  KArgs a1 = a0;
+  a1.real = lam_out;
+  e = cudaErrorInvalidValue;
+  switch (a0.nx) {
+#define FS_CASE(n) \
+  case n: e = adj_row_n<T, n>(a1, true, s); break;
+    FS_ADJ_SIZES(FS_CASE)
+#undef FS_CASE
+    default: break;
+  }
+  return e;
+}
+
+template <typename T, int NZ>
+cudaError_t adj_z_n(const KArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+  using Cfg = LineCfg<T, NZ>;
+  const int tk = line_tk<T, NZ>(a.nx);
+  const size_t smem = Cfg::HEAD + (size_t)3 * Cfg::TROWS * tk * sizeof(cplx<T>);
+  static unsigned d = 0;
+  cudaError_t e = allow_big_smem(fs_adj_z_kernel<T, NZ>, &d);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)(a.nx / 2 / tk), (unsigned)a.ny, (unsigned)a.nf);
+  fs_adj_z_kernel<T, NZ><<<grid, (unsigned)(tk * Cfg::TPL), smem, s>>>(a, tm);
+  return cudaGetLastError();
+}
+
+// Adjoint of one 3D step (five launches): x forward of lam', u, f(u) (the
+// 2D adjoint's row kernel over ny nz rows), y forward of the 3 nf slots (the
+// step's y pass), the z part (fs_adj_z_kernel), y inverse of the 2 nf result
+// slots, x inverse with the pointwise Hessian product.  tm_y: [slot nz + z][y]
+// [kx] over the adjoint slots; tm_z: [slot][z][y][kx].
+template <typename T>
+cudaError_t adjoint3_launch_t(const KArgs& a0, const CUtensorMap& tm_y, const CUtensorMap& tm_z, void* lam_out,
+                              cudaStream_t s) {
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (a0.nx) {
+#define FS_CASE(n) \
+  case n: e = adj_row_n<T, n>(a0, false, s); break;
+    FS_ADJ_SIZES(FS_CASE)
+#undef FS_CASE
+    default: break;
+  }
+  if (e != cudaSuccess) return e;
+  KArgs b = a0;
+  b.carry3 = 0;  // plain y transforms of every slot (no carried c)
+  b.plane0 = 0;
+  b.tc = 0;
+  constexpr bool f64 = sizeof(T) == 8;
+  e = f64 ? ypass_launch_f64(b, tm_y, -1, 3 * a0.nf, s) : ypass_launch_f32(b, tm_y, -1, 3 * a0.nf, s);
+  if (e != cudaSuccess) return e;
+  e = cudaErrorInvalidValue;
+  switch (a0.nz) {
+#define FS_CASE(n) \
+  case n: e = adj_z_n<T, n>(b, tm_z, s); break;
+    FS_LINE_SIZES(FS_CASE)
+#undef FS_CASE
+    default: break;
+  }
+  if (e != cudaSuccess) return e;
+  e = f64 ? ypass_launch_f64(b, tm_y, 1, 2 * a0.nf, s) : ypass_launch_f32(b, tm_y, 1, 2 * a0.nf, s);
   if (e != cudaSuccess) return e;
   KArgs a1 = a0;
   a1.real = lam_out;

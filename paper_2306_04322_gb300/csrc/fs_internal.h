@@ -109,6 +109,12 @@ cudaError_t energy_col_launch_f64(const KArgs& a, const CUtensorMap& tm, cudaStr
 // raw sensitivity sums; tm = tensor map over the adjoint slots.
 cudaError_t adjoint_launch_f32(const KArgs& a, const CUtensorMap& tm, void* lam_out, cudaStream_t s);
 cudaError_t adjoint_launch_f64(const KArgs& a, const CUtensorMap& tm, void* lam_out, cudaStream_t s);
+// Adjoint of one 3D step: the same slots and outputs; tm_y: [slot nz + z][y][kx]
+// and tm_z: [slot][z][y][kx] over the 3 nf adjoint slots.
+cudaError_t adjoint3_launch_f32(const KArgs& a, const CUtensorMap& tm_y, const CUtensorMap& tm_z, void* lam_out,
+                                cudaStream_t s);
+cudaError_t adjoint3_launch_f64(const KArgs& a, const CUtensorMap& tm_y, const CUtensorMap& tm_z, void* lam_out,
+                                cudaStream_t s);
 // Columns per CTA of the 2D column pass for this grid (the TMA box width).
 int col_tile_width(bool f64, int nx, int ny);
 // 3D passes (fs_k3d_f32.cu / fs_k3d_f64.cu): y transform of nslots slots of

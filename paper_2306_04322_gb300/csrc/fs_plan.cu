@@ -60,7 +60,8 @@ struct Member {
   void* alam = nullptr;   // lam' in (nf real fields)
   void* au = nullptr;     // u (nf real fields)
   void* aout = nullptr;   // lambda out (nf real fields)
-  CUtensorMap tmap_adj;
+  CUtensorMap tmap_adj;    // adjoint slots: 2D column tiles / 3D y-pass tiles
+  CUtensorMap tmap_adj_z;  // adjoint slots: 3D z lines
 };
 
 }  // namespace
@@ -1283,10 +1284,11 @@ fs_status fs_step_adjoint(fs_plan_t p, const void* const* u, const void* const* 
   if (!p) return fail(nullptr, FS_ERR_INVALID_ARG, "plan is NULL");
   if (!u || !lam_in || !lam_out) return fail(p, FS_ERR_INVALID_ARG, "field pointer array is NULL");
   Member& m = p->members[0];
-  if (p->members.size() != 1 || p->fd || m.prm.ndim != 2)
-    return fail(p, FS_ERR_UNSUPPORTED, "fs_step_adjoint is built for single 2D semi-implicit FS plans");
-  if (m.prm.n[0] > 1024 || m.prm.n[1] > 1024)
-    return fail(p, FS_ERR_UNSUPPORTED, "fs_step_adjoint supports axes up to 1024");
+  if (p->members.size() != 1 || p->fd)
+    return fail(p, FS_ERR_UNSUPPORTED, "fs_step_adjoint is built for single semi-implicit FS plans");
+  const bool three = m.prm.ndim == 3;
+  if (!three && (m.prm.n[0] > 1024 || m.prm.n[1] > 1024))
+    return fail(p, FS_ERR_UNSUPPORTED, "fs_step_adjoint supports 2D axes up to 1024");
   const size_t rs = p->f64 ? sizeof(double) : sizeof(float), cs = 2 * rs;
   const int nf = p->nf;
   if (!m.aspec) {
@@ -1296,17 +1298,31 @@ fs_status fs_step_adjoint(fs_plan_t p, const void* const* u, const void* const* 
     m.aout = plan_alloc(p, (size_t)nf * m.npts * rs);
     if (!m.aspec || !m.alam || !m.au || !m.aout) return fail(p, FS_ERR_OOM, "adjoint workspace allocation failed");
     EncodeTiledFn enc = encode_tiled();
-    const int units = p->f64 ? 2 : 1, nx = m.prm.n[0], ny = m.prm.n[1];
-    const int tk = fs::col_tile_width(p->f64, nx, ny);
+    const int units = p->f64 ? 2 : 1, nx = m.prm.n[0], ny = m.prm.n[1], nz = three ? m.prm.n[2] : 1;
     const cuuint64_t W = (cuuint64_t)(nx / 2) * units;
-    cuuint64_t dims[3] = {W, (cuuint64_t)ny, (cuuint64_t)(3 * nf)};
-    cuuint64_t strides[2] = {W * 8, W * 8 * ny};
-    cuuint32_t box[3] = {(cuuint32_t)(tk * units), (cuuint32_t)(ny < 256 ? ny : 256), 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    if (!enc || enc(&m.tmap_adj, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, m.aspec, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return fail(p, FS_ERR_CUDA, "adjoint tensor map");
+    auto encode = [&](CUtensorMap* map, cuuint32_t rank, const cuuint64_t* dims, const cuuint64_t* strides,
+                      const cuuint32_t* box) {
+      const cuuint32_t estr[4] = {1, 1, 1, 1};
+      return enc && enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, rank, m.aspec, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    // 2D: [slot][y][kx] column tiles; 3D: [slot nz + z][y][kx] tiles of the
+    // y passes and [slot][z][y][kx] z lines
+    const int tk = three ? (p->f64 ? fs::line_tile_width_f64(nx, ny) : fs::line_tile_width_f32(nx, ny))
+                         : fs::col_tile_width(p->f64, nx, ny);
+    const cuuint64_t dims[3] = {W, (cuuint64_t)ny, (cuuint64_t)nz * 3 * nf};
+    const cuuint64_t strides[2] = {W * 8, W * 8 * ny};
+    const cuuint32_t box[3] = {(cuuint32_t)(tk * units), (cuuint32_t)(ny < 256 ? ny : 256), 1};
+    bool ok = encode(&m.tmap_adj, 3, dims, strides, box);
+    if (ok && three) {
+      const int tkz = p->f64 ? fs::line_tile_width_f64(nx, nz) : fs::line_tile_width_f32(nx, nz);
+      const cuuint64_t dz[4] = {W, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)(3 * nf)};
+      const cuuint64_t sz[3] = {W * 8, W * 8 * ny, W * 8 * ny * nz};
+      const cuuint32_t bz[4] = {(cuuint32_t)(tkz * units), 1, (cuuint32_t)(nz < 256 ? nz : 256), 1};
+      ok = encode(&m.tmap_adj_z, 4, dz, sz, bz);
+    }
+    if (!ok) return fail(p, FS_ERR_CUDA, "adjoint tensor map");
   }
   cudaError_t e = cudaSuccess;
   for (int f = 0; f < nf && e == cudaSuccess; ++f) {
@@ -1323,13 +1339,16 @@ fs_status fs_step_adjoint(fs_plan_t p, const void* const* u, const void* const* 
   a.spec_bytes = (long long)3 * nf * m.slot_stride * (long long)cs;
   a.real_bytes = (long long)nf * m.npts * (long long)rs;
   a.aux = m.au;
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && three)
+    e = p->f64 ? fs::adjoint3_launch_f64(a, m.tmap_adj, m.tmap_adj_z, m.aout, p->stream)
+               : fs::adjoint3_launch_f32(a, m.tmap_adj, m.tmap_adj_z, m.aout, p->stream);
+  else if (e == cudaSuccess)
     e = p->f64 ? fs::adjoint_launch_f64(a, m.tmap_adj, m.aout, p->stream)
                : fs::adjoint_launch_f32(a, m.tmap_adj, m.aout, p->stream);
   for (int f = 0; f < nf && e == cudaSuccess; ++f)
     e = cudaMemcpyAsync(lam_out[f], (char*)m.aout + f * m.npts * rs, m.npts * rs, cudaMemcpyDefault, p->stream);
   if (e != cudaSuccess) return cuda_fail(p, e, "fs_step_adjoint");
-  p->last_launches = 3;
+  p->last_launches = three ? 5 : 3;
   if (grad) {
     double h[4];
     e = cudaMemcpyAsync(h, p->acc, sizeof(h), cudaMemcpyDeviceToHost, p->stream);

@@ -1,6 +1,7 @@
-"""The hand-written adjoint of the 2D step: one step against the oracle
-adjoint, and trajectory gradients (autograd + checkpointing) against central
-finite differences and the oracle."""
+"""The hand-written adjoint of the 2D and 3D steps: one step against the
+oracle adjoint (and, in 3D, against central differences of the GPU's own
+forward step), and trajectory gradients (autograd + checkpointing) against
+central finite differences and the oracle."""
 import numpy as np
 import pytest
 
@@ -62,6 +63,59 @@ def test_adjoint_step_fp32_matches_oracle(F, O):
     got, g = gpu_adjoint(F, pr, u, lam, "f32")
     assert rel_linf(got, ref) <= 2e-5
     assert np.max(np.abs(g - gref)) <= 2e-4 * np.max(np.abs(gref))
+
+
+@pytest.mark.parametrize("n,p,lap,dx", [((16, 16, 16), 1, 0, (1.0, 1.0, 1.0)), ((32, 16, 8), 2, 0, (1.0, 0.5, 1.0)),
+                                        ((16, 32, 16), 2, 2, (1.0, 1.0, 0.5)), ((8, 16, 32), 0, 1, (0.5, 1.0, 1.0))])
+def test_adjoint3_step_fp64_matches_oracle(F, O, n, p, lap, dx):
+    """3D: x, y, z transforms of the adjoint with the packed kx = 0 / Nyquist
+    column split into (kx, ky) modes, pair rows included."""
+    pr = I.Problem(n=n, dx=dx, p=p, lap=lap)
+    pr.dt = 5.0 * I.fd_stable_dt(pr)
+    rng = np.random.default_rng(7)
+    u = I.noise_fields(pr, seed=52, amp=0.3)
+    lam = rng.standard_normal(u.shape)
+    ref, gref = O.adjoint_step(pr, u, lam)
+    got, g = gpu_adjoint(F, pr, u, lam, "f64")
+    assert rel_linf(got, ref) <= 1e-11
+    assert np.max(np.abs(g - gref)) <= 1e-10 * np.max(np.abs(gref))
+
+
+def test_adjoint3_step_fp32_matches_oracle(F, O):
+    pr = I.Problem(n=(64, 64, 64), p=2)
+    pr.dt = 5.0 * I.fd_stable_dt(pr)
+    rng = np.random.default_rng(8)
+    u = I.noise_fields(pr, seed=53, amp=0.3).astype(np.float32)
+    lam = rng.standard_normal(u.shape).astype(np.float32)
+    ref, gref = O.adjoint_step(pr, u.astype(np.float64), lam.astype(np.float64))
+    got, g = gpu_adjoint(F, pr, u, lam, "f32")
+    assert rel_linf(got, ref) <= 2e-5
+    assert np.max(np.abs(g - gref)) <= 2e-4 * np.max(np.abs(gref))
+
+
+def test_adjoint3_is_the_transpose_of_the_gpu_step(F):
+    """<lam, (S(u + h v) - S(u - h v)) / 2h> with the GPU's FP64 3D step equals
+    <J^T lam, v> from the GPU adjoint: the adjoint transposes the forward
+    kernels themselves, not only the oracle."""
+    import torch
+    pr = I.Problem(n=(32, 16, 16), p=2)
+    pr.dt = 5.0 * I.fd_stable_dt(pr)
+    rng = np.random.default_rng(9)
+    u = I.noise_fields(pr, seed=54, amp=0.3)
+    lam = rng.standard_normal(u.shape)
+    v = rng.standard_normal(u.shape)
+
+    def step(x):
+        plan = F.Plan(pr, "f64")
+        plan.set_fields(torch.tensor(x, device="cuda"))
+        plan.step(1)
+        out = plan.get_fields().cpu().numpy()
+        plan.close()
+        return out
+    h = 1e-6
+    fd = np.sum(lam * (step(u + h * v) - step(u - h * v))) / (2 * h)
+    got, _ = gpu_adjoint(F, pr, u, lam, "f64")
+    assert np.sum(got * v) == pytest.approx(fd, rel=1e-7)
 
 
 def _loss(F, pr, theta, u0, target, precision, nsteps, every):
@@ -138,3 +192,24 @@ def test_trajectory_gradient_matches_oracle_adjoint(F, O):
         lam, g = O.adjoint_step(prt, states[n - 1], lam)
         gsum += g
     assert np.max(np.abs(th.grad.numpy() - gsum)) <= 1e-9 * np.max(np.abs(gsum))
+
+
+def test_adjoint3_under_the_bounds_checked_build(F, O):
+    """Every checked access of the 3D adjoint's five launches stays inside
+    its buffer (FS_DEBUG_BOUNDS build); results still match the oracle."""
+    from paper_2306_04322_gb300 import build as B
+    pr = I.Problem(n=(16, 8, 8), p=1)
+    pr.dt = 5.0 * I.fd_stable_dt(pr)
+    rng = np.random.default_rng(10)
+    u = I.noise_fields(pr, seed=55, amp=0.3)
+    lam = rng.standard_normal(u.shape)
+    ref, gref = O.adjoint_step(pr, u, lam)
+    L = F.bind(B.build(variant="bounds"))
+    saved = F._lib
+    F._lib = L
+    try:
+        got, g = gpu_adjoint(F, pr, u, lam, "f64")
+    finally:
+        F._lib = saved
+    assert rel_linf(got, ref) <= 1e-11
+    assert np.max(np.abs(g - gref)) <= 1e-10 * np.max(np.abs(gref))
