@@ -31,8 +31,8 @@
  *     must not run concurrently from several host threads.
  *   - Grid sizes: each axis a power of two, in [8, 2048] for 2D plans (the
  *     paper's finest grid is 2048^2, Table 1) and in [8, 1024] along x, [8,
- *     512] along y and z for 3D plans; batched members and the adjoint step
- *     take axes up to 1024.  Other sizes return FS_ERR_UNSUPPORTED.  p in
+ *     512] along y and z for 3D plans; batched members and the 2D adjoint
+ *     step take axes up to 1024.  Other sizes return FS_ERR_UNSUPPORTED.  p in
  *     [0, 4].  dt > 0; M = 0 or L = 0 is allowed.
  *   - Status codes are returned by value; fs_last_error() gives the text of
  *     the last failure on that plan (or on this thread for a NULL plan).
