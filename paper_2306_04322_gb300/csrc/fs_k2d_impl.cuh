@@ -45,6 +45,17 @@ cudaError_t row_launch_w(const KArgs& a, cudaStream_t s) {
   using Cfg = RowCfg<T, NX, W>;
   const long long reff = a.lines < Cfg::R ? a.lines : Cfg::R;
   const size_t smem = row_smem_bytes<T, NX, W>(a.nf);
+  // five fields at 32 values per thread (rows of 2048, wide rows of 1024):
+  // one warp per field (2048^2: 73.3 us against 76.8 us; with 16 values per
+  // thread, whose CTAs pack more densely, the 3D 256^3 x pass lost 5 %)
+  if constexpr (sizeof(T) == 4 && Cfg::E >= 32) {
+    if (a.nf == 5) {
+      static unsigned done5 = 0;
+      cudaError_t e = allow_big_smem(fs_row_kernel<T, NX, W, 5>, &done5);
+      if (e != cudaSuccess) return e;
+      return launch_pdl(fs_row_kernel<T, NX, W, 5>, dim3((unsigned)(a.lines / reff)), dim3(160u), smem, s, a);
+    }
+  }
   static unsigned done = 0;
   cudaError_t e = allow_big_smem(fs_row_kernel<T, NX, W>, &done);
   if (e != cudaSuccess) return e;

@@ -481,8 +481,12 @@ __device__ __forceinline__ bool row_body(const KArgs& a, long long rb, unsigned 
 }
 
 
-template <typename T, int NX, bool W = false>
-__global__ void __launch_bounds__(RowCfg<T, NX, W>::THREADS, RowCfg<T, NX, W>::MIN_BLOCKS)
+// NW warps per CTA: 4 (fields w, w + 4, ...), or 5 for five fields in FP32
+// at 32 values per thread, one warp per field, so no warp carries two
+// transforms per phase (register budget of three CTAs per SM).
+template <typename T, int NX, bool W = false, int NW = 4>
+__global__ void __launch_bounds__(32 * NW, NW == 4 ? RowCfg<T, NX, W>::MIN_BLOCKS
+                                                   : (RowCfg<T, NX, W>::E >= 32 ? 3 : 5))
     fs_row_kernel(KArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
