@@ -178,6 +178,8 @@ class Slab:
         F.fs_slab_sync(self.h)
 
     def close(self):
+        # the views alias the slab's device memory: drop them before it is freed
+        self.send = self.recv = self.colspec = None
         if self.h is not None and self.h.value:
             F.fs_slab_destroy(self.h)
         self.h = None
