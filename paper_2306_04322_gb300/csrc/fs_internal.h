@@ -95,10 +95,11 @@ bool col2_supported(int ny, int nf);
 // Fused step (pass form 4, fs_step2_f32.cu): `nsteps` steady-state steps
 // (mode 0) of a 2D FP32 plan in one cooperative launch, the pair-form row
 // pass and the warp-per-column pass separated by grid-wide barriers on the
-// two counters at gsync (zero between launches).  Square grids of 256, 512
-// or 1024 points, nf <= 4; needs tw_row2, tw_col2 and the two-column tensor
-// map.  cudaErrorNotSupported for other requests.
+// counters at gsync (kStep2SyncBytes, zero between launches).  Square grids
+// of 256, 512 or 1024 points, nf <= 4; needs tw_row2, tw_col2 and the
+// two-column tensor map.  cudaErrorNotSupported for other requests.
 bool step2_supported(int nx, int ny, int nf);
+constexpr size_t kStep2SyncBytes = 4096;  // counters of the fused step's grid barriers (zeroed)
 cudaError_t step2_launch_f32(const KArgs& a, const CUtensorMap& tm, unsigned* gsync, int nsteps, cudaStream_t s);
 // Free-energy diagnostic, 2D (row pass mode 3 does the chemical sum and the
 // x transforms): y transforms and sums of w K2 |phi^|^2 per field.

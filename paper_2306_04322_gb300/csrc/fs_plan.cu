@@ -543,7 +543,7 @@ fs_status read_flag(fs_plan* p) {
   if (f) {
     cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream);
     if (f & fs::FS_FLAG_TIMEOUT) {
-      cudaMemsetAsync(p->gsync, 0, 2 * sizeof(unsigned), p->stream);  // a fused step may have left a barrier open
+      cudaMemsetAsync(p->gsync, 0, fs::kStep2SyncBytes, p->stream);  // a fused step may have left a barrier open
       return fail(p, FS_ERR_TIMEOUT, "a bounded device wait timed out");
     }
     if (f & fs::FS_FLAG_NONFINITE) return fail(p, FS_ERR_NONFINITE, "non-finite value in the fields");
@@ -1029,7 +1029,7 @@ fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc
   }
   p->flag = (int*)plan_alloc(p, 256);
   p->acc = (double*)plan_alloc(p, 256);
-  p->gsync = (unsigned*)plan_alloc(p, 256);
+  p->gsync = (unsigned*)plan_alloc(p, fs::kStep2SyncBytes);
   if (!p->flag || !p->acc || !p->gsync) {
     plan_free_all(p);
     delete p;
@@ -1047,7 +1047,7 @@ fs_status create_common(const fs_params* each, int count, void* stream, fs_alloc
     if (e == cudaSuccess && !encode_col_map(p->members[i], p->nf + 1, p->f64)) e = cudaErrorInvalidValue;
   }
   if (e == cudaSuccess) e = cudaMemset(p->flag, 0, 256);
-  if (e == cudaSuccess) e = cudaMemset(p->gsync, 0, 256);
+  if (e == cudaSuccess) e = cudaMemset(p->gsync, 0, fs::kStep2SyncBytes);
   if (e != cudaSuccess) {
     fs_status s = cuda_fail(nullptr, e, "plan tables");
     cudaFreeHost(p->host_flag);

@@ -18,7 +18,7 @@ namespace fs {
 
 namespace {
 
-constexpr uint32_t kGridWaitPolls = 1u << 24;  // with a 64 ns back-off: about a second
+constexpr uint32_t kGridWaitPolls = 1u << 25;  // with a 32 ns back-off: about a second
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
@@ -29,30 +29,49 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// Grid-wide barrier of a cooperative launch (all CTAs resident): sync[0]
-// counts arrivals, sync[1] is the generation the waiters watch.  Returns
-// false in every thread of the CTA if the wait gave up after `limit` polls
-// (FS_FLAG_TIMEOUT is set); the counters are then reset by the host.
+// Grid-wide barrier of a cooperative launch (all CTAs resident), two
+// levels so that no counter sees more than a few dozen atomics: CTA b
+// arrives at group counter b % kGroups; the last arrival of a group arrives
+// at the top counter; the last arrival there advances the generation the
+// waiters watch.  Counters sit on their own 128-byte lines of `sync` (word
+// 32 g for group g, 32 kGroups for the top, 32 (kGroups + 1) for the
+// generation).  Returns false in every thread of the CTA if the wait gave up
+// after `limit` polls (FS_FLAG_TIMEOUT is set); the host then zeroes the
+// counters.
+constexpr int kGroups = 16;
+constexpr int kSyncWords = 32 * (kGroups + 2);
+
 __device__ __forceinline__ bool grid_barrier(unsigned* sync, unsigned nblocks, uint32_t limit, int* flag) {
   fence_proxy_async_global();
   __syncthreads();
   bool ok = true;
   if (threadIdx.x == 0) {
-    const unsigned gen = ld_acquire_gpu(&sync[1]);  // cannot advance before this CTA arrives
+    unsigned* gen_p = sync + 32 * (kGroups + 1);
+    const unsigned gen = ld_acquire_gpu(gen_p);  // cannot advance before this CTA arrives
+    const unsigned groups = nblocks < (unsigned)kGroups ? nblocks : (unsigned)kGroups;
+    const unsigned g = blockIdx.x % groups;
+    const unsigned in_group = nblocks / groups + (g < nblocks % groups ? 1u : 0u);
     __threadfence();
-    if (atomicAdd(&sync[0], 1u) == nblocks - 1) {
-      atomicExch(&sync[0], 0u);
+    bool last = false;
+    if (atomicAdd(&sync[32 * g], 1u) == in_group - 1) {
+      atomicExch(&sync[32 * g], 0u);
       __threadfence();
-      atomicAdd(&sync[1], 1u);
-    } else {
+      if (atomicAdd(&sync[32 * kGroups], 1u) == groups - 1) {
+        atomicExch(&sync[32 * kGroups], 0u);
+        __threadfence();
+        atomicAdd(gen_p, 1u);
+        last = true;
+      }
+    }
+    if (!last) {
       uint32_t i = 0;
-      while (ld_acquire_gpu(&sync[1]) == gen) {
+      while (ld_acquire_gpu(gen_p) == gen) {
         if (i++ >= limit) {
           ok = false;
           atomicOr(flag, FS_FLAG_TIMEOUT);
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     __threadfence();
