@@ -77,3 +77,16 @@ def test_table2_study_small(X):
     fs = {row["grid"]: row for row in rows if row["scheme"] == "FS"}
     assert fs[16]["E_eta"] > fs[32]["E_eta"] > 0.0
     assert {row["scheme"] for row in rows} == {"FS", "FSFD2", "FSFD4", "FD"}
+
+
+def test_slab_study_small(X):
+    """The slab timing study on a small grid: per-rank times are positive and
+    the exchange bytes follow the layout."""
+    r = X.slab_study(steps=3, grids=(64,), ranks=(1, 2))
+    rows = r["rows"]
+    assert [row["ranks"] for row in rows] == [1, 2]
+    for row in rows:
+        assert row["row_ms_per_rank"] > 0 and row["col_ms_per_rank"] > 0 and row["plan_step_ms"] > 0
+    assert rows[0]["exchange_bytes_per_rank"] == 0
+    # R = 2, p = 2: (2 nf + 1) (R - 1) N s / R^2 = 7 * 64 * 64 * 4 / 4
+    assert rows[1]["exchange_bytes_per_rank"] == 7 * 64 * 64 * 4 // 4
