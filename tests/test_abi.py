@@ -148,3 +148,35 @@ def test_3d_axis_limits(L):
     assert b"3D grids" in L.fs_last_error(None)
     P.n[0], P.n[1] = 64, 1024
     assert L.fs_plan_create(ctypes.byref(P), None, ctypes.byref(h)) == F.FS_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("kw,rank,nranks,status", [
+    ({}, 0, 3, F.FS_ERR_UNSUPPORTED),            # not a power of two
+    ({}, 2, 2, F.FS_ERR_INVALID_ARG),            # rank out of range
+    ({}, -1, 2, F.FS_ERR_INVALID_ARG),
+    ({}, 0, 16, F.FS_ERR_UNSUPPORTED),           # 64 / 16 < 8 rows per rank
+    ({"precision": F.FS_F32_TC_TF32}, 0, 2, F.FS_ERR_UNSUPPORTED),
+    ({"scheme": F.FS_SCHEME_EXPLICIT_FD}, 0, 2, F.FS_ERR_UNSUPPORTED),
+    ({"ndim": 3}, 0, 2, F.FS_ERR_UNSUPPORTED),
+    ({"dt": -1.0}, 0, 2, F.FS_ERR_INVALID_ARG),  # refused by the row plan's validation
+])
+def test_slab_requests_rejected_without_cuda(L, kw, rank, nranks, status):
+    """fs_slab_create validates before any CUDA call (include/fs_slab.h)."""
+    P = good_params(**kw)
+    if kw.get("ndim") == 3:
+        P.n[2], P.dx[2] = 64, 1.0
+    h = ctypes.c_void_p(123)
+    assert L.fs_slab_create(ctypes.byref(P), rank, nranks, None, ctypes.byref(h)) == status
+    assert h.value is None
+    assert L.fs_slab_last_error(None)
+
+
+def test_slab_null_handles(L):
+    h = ctypes.c_void_p()
+    assert L.fs_slab_create(None, 0, 1, None, ctypes.byref(h)) == F.FS_ERR_INVALID_ARG
+    P = good_params()
+    assert L.fs_slab_create(ctypes.byref(P), 0, 1, None, None) == F.FS_ERR_INVALID_ARG
+    for fn in ("fs_slab_row_pass", "fs_slab_col_pass", "fs_slab_sync"):
+        assert getattr(L, fn)(None) == F.FS_ERR_INVALID_ARG
+    assert L.fs_slab_info_get(None, None) == F.FS_ERR_INVALID_ARG
+    assert L.fs_slab_destroy(None) == F.FS_OK
